@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the TPO hot path on one GB300 (and N independent replicas under torchrun).
+
+A step is one full solve (Algorithms 1-3 and the objective) of the large planted-partition
+workload: |U| = 2,000,000, |V| = 5,000,000, 50M edge draws (Chung-Lu exponent 2.2 on both
+sides, 60/40 mixing), dense Gaussian-mixture attributes d = 128 stored as BF16, k = 100,
+alpha = 0.9, gamma = 10, T_f = 5, T_g = 20. Inputs are synthetic (seeded generator) and far
+larger than L2 (the graph alone is ~1.3 GB, a solve touches ~60 GB).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0. `value` = solves/s of the whole job with the graph resident in
+HBM; `e2e` = the same through the C ABI from pinned host buffers (graph upload, solve, labels
+back, graph freed, every step). `roofline` covers the propagation SpMMs (the dominant kernels),
+timed by CUDA events inside the library on the launch stream. The reference arm times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("TPO iterations/s and SpMM HBM GB/s at |U|=2M; solves/s + p99 latency "
+          "(served vs plain)")
+WORKLOAD = dict(workload="planted ABG |U|=2M |V|=5M 50M edge draws, Chung-Lu 2.2, 60/40 mixing, "
+                         "dense BF16 attributes d=128, k=100, alpha=0.9, gamma=10, T_f=5, T_g=20",
+                n_u=2_000_000, n_v=5_000_000, d=128, k=100)
+PARAMS = dict(k=100, alpha=0.9, gamma=10, d=128, t_f=5, t_g=20, seed=0)
+ORACLE_SCALES = (0.01, 0.02)   # oracle sample sizes (fraction of the full workload)
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during a timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"abg_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def gpu_id_for_smi(local_rank: int) -> str:
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        return ids[local_rank] if local_rank < len(ids) else str(local_rank)
+
+
+def propagation_bytes(g, d: int, gamma: int) -> float:
+    """Algorithmic bytes of gamma propagation rounds (both SpMMs): per round, each SpMM reads
+    nnz (index + value) and one gathered d-wide row per edge, plus its row pointers and row
+    list; the first product gathers BF16 X rows, the rest FP32 Z rows; the second product also
+    reads the X restart rows (BF16) and writes Z; the first writes W."""
+    nnz, n_u, n_v = g.nnz, g.n_u, g.n_v
+    per_spmm_index = nnz * 8
+    total = 0.0
+    for r in range(gamma):
+        zin = 2 if r == 0 else 4
+        total += per_spmm_index + nnz * d * zin + n_v * (8 + 4) + n_v * d * 4     # W = L^T Z
+        total += per_spmm_index + nnz * d * 4 + n_u * (8 + 4) + n_u * d * (2 + 4)  # Z = ...
+    return total
+
+
+def csc_of(g):
+    order = np.argsort(g.v_idx, kind="stable")
+    v_ptr = np.zeros(g.n_v + 1, dtype=np.int64)
+    np.cumsum(np.bincount(g.v_idx, minlength=g.n_v), out=v_ptr[1:])
+    rows = np.repeat(np.arange(g.n_u, dtype=np.int32), np.diff(g.u_ptr))
+    return v_ptr, rows[order], (g.w[order] if g.w is not None else None)
+
+
+class PinnedGraph:
+    """The generator's arrays copied into page-locked host memory (for the e2e arm)."""
+
+    def __init__(self, g, csc):
+        import torch
+
+        def pin(a):
+            return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+        self._keep = [pin(a) for a in (g.u_ptr, g.v_idx, g.w, g.x, csc[0], csc[1], csc[2])]
+        arr = [None if t is None else t.numpy() for t in self._keep]
+        self.n_u, self.n_v, self.d_u, self.x_kind = g.n_u, g.n_v, g.d_u, g.x_kind
+        self.u_ptr, self.v_idx, self.w, self.x = arr[0], arr[1], arr[2], arr[3]
+        self.x_ptr = self.x_idx = self.x_val = None
+        self.csc = (arr[4], arr[5], arr[6])
+        self.h2d_bytes = sum(int(a.nbytes) for a in arr if a is not None)
+
+
+def oracle_sample(seed: int = 0) -> dict:
+    """Time the FP64 oracle on two small instances of the workload generator and extrapolate
+    linearly to the full size (every phase is linear in |U| and |E| at fixed d and k)."""
+    import synth
+    from oracle import tpo
+    times = []
+    for sc in ORACLE_SCALES:
+        g = synth.make_config3(seed=seed, scale=sc)
+        t0 = time.perf_counter()
+        tpo.tpo(g, **PARAMS)
+        times.append(time.perf_counter() - t0)
+    (s0, s1), (t0, t1) = ORACLE_SCALES, times
+    slope = (t1 - t0) / (s1 - s0)
+    est = max(t1, t1 + slope * (1.0 - s1))
+    return dict(seconds_full_est=est, sample_seconds=times,
+                sample=(f"full oracle solves of the same generator at {s0:g} and {s1:g} of the "
+                        f"workload (|U|={int(2e6 * s0)} and {int(2e6 * s1)}, k=100), "
+                        f"extrapolated linearly in size to |U|=2M"),
+                cores=os.cpu_count())
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(seed=0)
+        if i >= args.warmup:
+            vals.append(1.0 / r["seconds_full_est"])
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism="cpu oracle"),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    g = synth.make_config3(seed=rank, scale=args.scale)
+    csc = csc_of(g)
+    p = abg.params(**PARAMS)
+    stream = torch.cuda.current_stream()
+    graph = abg.abg_create(g, device=local_rank, stream=stream, csc=csc)
+    labels = torch.empty(g.n_u, dtype=torch.int32).pin_memory().numpy()
+
+    for _ in range(args.warmup):
+        abg.abg_cluster(graph, p, labels, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_id_for_smi(local_rank))
+    barrier()
+    l0 = abg.abg_launch_count()
+    results = []
+    with sampler:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, res = abg.abg_cluster(graph, p, labels, stream)
+            results.append(res)
+        ev1.record(stream)
+        barrier()
+    launches = abg.abg_launch_count() - l0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    clocks = sampler.summary()
+    prop_ms = statistics.median(r.ms_phase[1] for r in results)
+    phase_ms = [statistics.median(r.ms_phase[i] for r in results) for i in range(6)]
+    graph.close()
+
+    # ---- end to end through the C ABI from pinned host memory ----
+    pin = PinnedGraph(g, csc)
+    for _ in range(1):
+        gh = abg.abg_create(pin, device=local_rank, stream=stream, csc=pin.csc)
+        abg.abg_cluster(gh, p, labels, stream)
+        gh.close()
+    barrier()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gh = abg.abg_create(pin, device=local_rank, stream=stream, csc=pin.csc)
+        abg.abg_cluster(gh, p, labels, stream)
+        gh.close()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak()
+    pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"])
+    achieved = pbytes / (prop_ms / 1e3) / 1e9
+    value = world * args.steps / elapsed
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, nnz=int(g.nnz), parallelism=f"{world} independent solves "
+                       "(one graph per rank)" if world > 1 else "single GPU",
+                       l2="inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"),
+        "tpo_prop_iters_per_s": PARAMS["gamma"] / (prop_ms / 1e3),
+        "spmm_hbm_gbs": achieved,
+        "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
+                              "objective"], phase_ms)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "propagation SpMMs (k_spmm_rows/chunks/reduce, gamma rounds)",
+                     "peak_kind": peak_kind},
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(seed=0)
+        line["cpu_baseline"] = {"value": 1.0 / r["seconds_full_est"], "unit": "solves/s",
+                                "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * abg.h — C ABI of a GB300 (sm_103a) implementation of TPO clustering on
+ * attributed bipartite graphs (Yang et al., "Effective Clustering on Large
+ * Attributed Bipartite Graphs", KDD'24, arXiv 2405.11922).
+ *
+ * Conventions for every call
+ *   - Returns int status: ABG_OK (0), ABG_PENDING (1) or a negative error.
+ *     Nothing throws across this boundary; abg_strerror() names the code and
+ *     abg_last_error() gives a one-line detail of the last failure on the
+ *     calling thread.
+ *   - "host" pointers are read with plain loads; "device" pointers must be
+ *     device memory of the graph's device (cudaMalloc / a PyTorch CUDA tensor).
+ *     Where a pointer may be either, cudaMemcpy with cudaMemcpyDefault is used.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Step calls
+ *     only enqueue work on it; abg_cluster synchronises it before returning.
+ *   - Dense matrices are row-major with an explicit leading dimension `ld*`
+ *     (elements between consecutive rows), ld >= width and ld a multiple of 4
+ *     (16-byte rows for float). Every device matrix must be 16-byte aligned.
+ *   - Sizes: |U|, |V| < 2^31, nnz < 2^62, 1 <= d <= 1024, 1 <= k <= 128.
+ *   - The library allocates its own device memory (stream-ordered, from a
+ *     private pool per device); callers own the buffers they pass in.
+ *
+ * Notation follows the paper: B_U (|U| x |V|) the weighted adjacency,
+ * D_U / D_V the weighted degrees (Section 2.1), L_U = D_U^-1/2 B_U D_V^-1/2
+ * (Eq. 7), X_U the U attributes, Z_U / Z_hat the propagated / row-normalised
+ * features (Eqs. 6, 2), R the random-feature matrix (Eqs. 13-14), Phi and H the
+ * NMF factors (Eqs. 11, 16-18), Y the normalised cluster indicator (Eq. 10).
+ */
+#ifndef ABG_H
+#define ABG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ABG_API __attribute__((visibility("default")))
+#else
+#define ABG_API
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define ABG_OK 0
+#define ABG_PENDING 1            /* abg_poll: the job has not finished yet      */
+#define ABG_EINVAL (-1)          /* bad argument or malformed input             */
+#define ABG_ENOMEM (-2)          /* device allocation failed                    */
+#define ABG_EDEVICE (-3)         /* CUDA error (launch, copy, bounded wait)     */
+#define ABG_ENOTADMITTED (-4)    /* job footprint exceeds the server budget     */
+#define ABG_ETIMEDOUT (-5)       /* abg_poll: timeout elapsed                   */
+#define ABG_ENOTFOUND (-6)       /* unknown request id                          */
+#define ABG_ECANCELLED (-7)      /* request cancelled / server shut down        */
+#define ABG_ENUMERIC (-8)        /* non-finite values or a singular Gram matrix */
+
+/* ---- attribute storage kinds (abg_graph_desc.x_kind) --------------------- */
+#define ABG_X_DENSE_F32 0        /* x: float [n_u][d_u]                          */
+#define ABG_X_DENSE_BF16 1       /* x: uint16 bfloat16 bit patterns [n_u][d_u]   */
+#define ABG_X_CSR_F32 2          /* x_ptr[n_u+1], x_idx[x_nnz], x_val[x_nnz]     */
+
+/* ---- random streams of the counter-based generator ----------------------- */
+/* Gaussian entry e of a matrix drawn on stream s with key `seed` comes from
+ * Philox4x32-10 (Salmon et al., SC'11) at counter (b mod 2^32, b >> 32, s, 0),
+ * b = e / 4, key (seed mod 2^32, seed >> 32), through Box-Muller on the two
+ * word pairs (u = (x + 0.5) 2^-32; cos / sin of 2 pi u_b times
+ * sqrt(-2 ln u_a)); entry e takes output e mod 4. */
+#define ABG_STREAM_G 1           /* Algorithm 1: G (d x d) -> Q                  */
+#define ABG_STREAM_OMEGA_R 2     /* Algorithm 2: test matrix of the SVD of R     */
+#define ABG_STREAM_OMEGA_X 3     /* Section 3.2.1: test matrix of the SVD of X_U */
+
+typedef struct abg_graph abg_graph;
+
+/* Input graph (Definition 1, Section 2.1). All pointers are HOST memory and
+ * are copied; the caller keeps ownership. The CSR must have a monotone u_ptr
+ * with u_ptr[0] = 0, u_ptr[n_u] = nnz and v_idx in [0, n_v). w == NULL means
+ * unit weights; weights must be finite and > 0. The CSC (v_ptr, u_idx, w_t)
+ * is optional (all three NULL: it is built by a stable counting sort); when
+ * given it must hold exactly the same edges. */
+typedef struct {
+  int64_t n_u, n_v, nnz;
+  const int64_t* u_ptr;
+  const int32_t* v_idx;
+  const float* w;
+  const int64_t* v_ptr;
+  const int32_t* u_idx;
+  const float* w_t;
+  int32_t d_u;
+  int32_t x_kind;
+  const void* x;
+  const int64_t* x_ptr;
+  const int32_t* x_idx;
+  const float* x_val;
+  int32_t device;
+  int32_t reserved;
+} abg_graph_desc;
+
+/* Method parameters (Table 1). d = 0 means d = d_u (no attribute reduction,
+ * "TPO (d = d_U)"); 1 <= d < d_u turns on the SVD reduction of Section 3.2.1.
+ * alpha in [0, 1), gamma >= 0, 1 <= k <= min(|U|, 2d, 128), t_f, t_g >= 0,
+ * oversample >= 0 and power_iters >= 0 configure the truncated randomized
+ * SVDs (Halko-Martinsson-Tropp subspace iteration). */
+typedef struct {
+  int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
+  int32_t reserved0;
+  double alpha;
+  uint64_t seed;
+} abg_params;
+
+/* Per-solve report. objective = Eq. 8 with s(u_i,u_j) := R[i].R[j] (minimised);
+ * trace_obj = Tr(Y^T R R^T Y) (maximised, Lemma obj3); both FP64. min_margin =
+ * smallest top1 - top2 score gap of the last NCI pass (Eq. 21). */
+typedef struct {
+  double objective;
+  double trace_obj;
+  double min_margin;
+  int32_t last_changes;     /* labels changed by the last NCI pass            */
+  int32_t empty_clusters;   /* clusters left empty (Eq. 23 leaves them zero)  */
+  int32_t clamped_rows;     /* rows with R'[i].r <= 0 before Eq. 14            */
+  int32_t chol_breakdowns;  /* Gram pivots that were not positive             */
+  /* device time (CUDA events on `stream`, ms) of: attribute preparation (incl.
+   * the Eq. 15 reduction), the propagation of Algorithm 1 (both SpMMs, all
+   * gamma rounds, Eq. 2), Q and the random features (Eqs. 13-14), the SVD
+   * seeding + NMF (Algorithm 2), NCI generation (Algorithm 3), the objective */
+  float ms_phase[6];
+} abg_result;
+
+ABG_API const char* abg_strerror(int status);
+ABG_API const char* abg_last_error(void);
+ABG_API void abg_params_default(abg_params* p);   /* k=2, gamma=6, alpha=.6, t_f=5, t_g=20, p=10, q=4 */
+/* Number of CUDA kernels this library has launched in the calling process so
+ * far (a diagnostic counter; every launch site increments it). */
+ABG_API int64_t abg_launch_count(void);
+
+/* ---- graph lifetime ------------------------------------------------------ */
+
+/* Validate and upload one ABG, build its CSC if absent, compute the degree
+ * scales D^-1/2 (a zero degree gets 0) and the L_U values of Eq. 7 in both
+ * CSR and CSC order. Errors: ABG_EINVAL (malformed CSR/CSC, weights, sizes),
+ * ABG_ENOMEM, ABG_EDEVICE. On error *out is NULL. */
+ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out);
+ABG_API void abg_destroy(abg_graph* g);
+ABG_API int64_t abg_graph_footprint(const abg_graph* g);   /* device bytes held */
+ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p); /* bytes one solve adds */
+
+/* ---- the whole method ---------------------------------------------------- */
+
+/* Algorithms 1-3 end to end on `g`: labels[n_u] (host or device memory) get
+ * cluster ids in [0, k); `res` (host, may be NULL) the report. Synchronises
+ * `stream`. Errors: ABG_EINVAL (parameters), ABG_ENOMEM, ABG_EDEVICE,
+ * ABG_ENUMERIC. */
+ABG_API int abg_cluster(abg_graph* g, const abg_params* p, void* stream, int32_t* labels,
+                        abg_result* res);
+
+/* ---- individual steps (device buffers owned by the caller) --------------- */
+
+/* Eq. 15 / Section 3.2.1: x_out[n_u][ldo] = Gamma Sigma, the top-d SVD of the
+ * graph's X_U (randomized, stream ABG_STREAM_OMEGA_X, each left vector signed
+ * so that its entries sum >= 0). */
+ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversample,
+                                  int32_t power_iters, uint64_t seed, float* x_out, int64_t ldo,
+                                  void* stream);
+
+/* Algorithm 1 propagation (Eq. 6 in the restart form Z_0 = (1-a) X,
+ * Z <- (1-a) X + a L (L^T Z), gamma times), then Eq. 2: zhat[n_u][ldz] holds
+ * the row-normalised Z_U (a zero row stays zero). x = NULL uses the graph's
+ * own dense attributes (d must equal d_u); otherwise x[n_u][ldx] (device,
+ * float) is the attribute matrix of width d (e.g. abg_reduce_attributes). */
+ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32_t d,
+                          double alpha, int32_t gamma, float* zhat, int64_t ldz, void* stream);
+
+/* Algorithm 1: q_out[d][d] (device, double) = the orthogonal factor of the QR
+ * of G ~ N(0,1)^{d x d} drawn on ABG_STREAM_G, with diag(R_qr) > 0. */
+ABG_API int abg_orthogonal_matrix(uint64_t seed, int32_t d, double* q_out, void* stream);
+
+/* Eqs. 13-14: r_out[n][ldr] = R for zhat[n][ldz] (width d) and the orthogonal
+ * matrix of abg_orthogonal_matrix(seed, d). clamped (host, may be NULL) gets
+ * the number of rows whose R'[i].r was <= 0. */
+ABG_API int abg_random_features(const float* zhat, int64_t n, int32_t d, int64_t ldz,
+                                uint64_t seed, float* r_out, int64_t ldr, int32_t* clamped,
+                                void* stream);
+
+/* Algorithm 2 seeding (Eq. 18): truncated randomized SVD of r[n][m] (stream
+ * ABG_STREAM_OMEGA_R), phi_out[n][ldphi] = max(Gamma, 0), h_out[m][ldh] =
+ * max(Psi Sigma, 0), sigma_out[k] (device, double, may be NULL). */
+ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k,
+                             int32_t oversample, int32_t power_iters, uint64_t seed,
+                             float* phi_out, int64_t ldphi, float* h_out, int64_t ldh,
+                             double* sigma_out, void* stream);
+
+/* Algorithm 2 loop: t_f times H by Eq. 16 then Phi by Eq. 17, in place on
+ * phi[n][ldphi] and h[m][ldh] (max(numerator, 0); a non-positive denominator
+ * sets the entry to 0). */
+ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k, int32_t t_f,
+                     float* phi, int64_t ldphi, float* h, int64_t ldh, void* stream);
+
+/* Algorithm 3: T = I; t_g times l* = argmax_l Phi[i].T[:, l] (ties -> lowest
+ * l), Y by Eqs. 22-23, T <- Phi^T Y. labels_out[n] (device int32),
+ * margin_out[n] (device float, may be NULL: top1 - top2 of the last pass),
+ * t_out[k][k] (device double, may be NULL: T after the last pass),
+ * last_changes (host, may be NULL). */
+ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32_t t_g,
+                    int32_t* labels_out, float* margin_out, double* t_out,
+                    int32_t* last_changes, void* stream);
+
+/* Eq. 8 with s := R R^T through per-cluster sums (FP64): obj (host) gets
+ * {objective, trace_obj}. labels must lie in [0, k). */
+ABG_API int abg_objective(const float* r, int64_t n, int32_t m, int64_t ldr,
+                          const int32_t* labels, int32_t k, double* obj, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABG_H */

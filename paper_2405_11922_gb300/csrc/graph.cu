@@ -1,0 +1,426 @@
+// Graph ingestion (Section 2.1, Eq. 7): validation, upload, CSC construction,
+// weighted degrees, the D^-1/2 scales and the L_U values in CSR and CSC order,
+// and the row schedules the two SpMMs use. Also the library-wide error text
+// and the pooled stream-ordered allocator.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace abg {
+
+static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  return e == cudaErrorMemoryAllocation ? ABG_ENOMEM : ABG_EDEVICE;
+}
+
+// ---- private memory pool per device -------------------------------------------
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static int pool_for_current(cudaMemPool_t* out) {
+  int dev = 0;
+  ABG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return ABG_EDEVICE;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    ABG_CUDA(cudaMemPoolCreate(&g_pool[dev], &props));
+    uint64_t thr = UINT64_MAX;
+    ABG_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  *out = g_pool[dev];
+  return ABG_OK;
+}
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool;
+  ABG_TRY(pool_for_current(&pool));
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %zu bytes failed (%s)", bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return ABG_ENOMEM;
+  }
+  return ABG_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s) {
+  if (g->n_blocks >= 32) {
+    set_error("internal: too many graph blocks");
+    return ABG_ENOMEM;
+  }
+  ABG_TRY(dev_alloc(p, bytes, s));
+  g->blocks[g->n_blocks++] = *p;
+  g->footprint += (int64_t)bytes;
+  return ABG_OK;
+}
+
+// ---- kernels --------------------------------------------------------------------
+
+// Weighted degree of each row (Section 2.1), FP64 sums, one warp per row; then
+// the scale D^-1/2 with 0 for a zero degree.
+__global__ void k_row_scale(const int64_t* __restrict__ ptr, const float* __restrict__ w,
+                            int64_t rows, float* __restrict__ scale) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  int64_t b = ptr[row], e = ptr[row + 1];
+  double acc = 0.0;
+  for (int64_t j = b + lane; j < e; j += 32) acc += w ? (double)w[j] : 1.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) scale[row] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
+}
+
+// L values (Eq. 7) of one storage order: val[e] = w[e] * s_row[row] * s_col[col[e]].
+__global__ void k_l_values(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const float* __restrict__ w, int64_t rows,
+                           const float* __restrict__ s_row, const float* __restrict__ s_col,
+                           float* __restrict__ val) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  int64_t b = ptr[row], e = ptr[row + 1];
+  double sr = (double)s_row[row];
+  for (int64_t j = b + lane; j < e; j += 32) {
+    double wj = w ? (double)w[j] : 1.0;
+    val[j] = (float)(wj * sr * (double)s_col[col[j]]);
+  }
+}
+
+// Column counts of the CSR (to verify a caller-given CSC).
+__global__ void k_col_count(const int32_t* __restrict__ col, int64_t nnz, int* __restrict__ cnt) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+       j += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[j]], 1);
+}
+
+__global__ void k_count_mismatch(const int64_t* __restrict__ ptr, const int* __restrict__ cnt,
+                                 int64_t rows, int* __restrict__ bad) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    if ((int64_t)cnt[r] != ptr[r + 1] - ptr[r]) atomicAdd(bad, 1);
+}
+
+}  // namespace abg
+
+using namespace abg;
+
+// ---- host helpers -----------------------------------------------------------------
+
+static int validate_csr(const int64_t* ptr, const int32_t* idx, const float* w, int64_t rows,
+                        int64_t cols, int64_t nnz, const char* name) {
+  ABG_CHECK(ptr && idx, "%s: null CSR arrays", name);
+  ABG_CHECK(ptr[0] == 0 && ptr[rows] == nnz, "%s: ptr[0] must be 0 and ptr[rows] = nnz", name);
+  for (int64_t r = 0; r < rows; ++r)
+    ABG_CHECK(ptr[r + 1] >= ptr[r], "%s: ptr not monotone at row %lld", name, (long long)r);
+  for (int64_t j = 0; j < nnz; ++j)
+    ABG_CHECK(idx[j] >= 0 && idx[j] < cols, "%s: index %d out of range at %lld", name, idx[j],
+              (long long)j);
+  if (w)
+    for (int64_t j = 0; j < nnz; ++j)
+      ABG_CHECK(std::isfinite(w[j]) && w[j] > 0.f, "%s: weight %g at %lld not finite/positive",
+                name, (double)w[j], (long long)j);
+  return ABG_OK;
+}
+
+// Stable counting sort CSR -> CSC (deterministic edge order inside each column:
+// increasing row), parallel over row ranges with per-thread column offsets.
+static void build_csc(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t* u_ptr,
+                      const int32_t* v_idx, const float* w, std::vector<int64_t>& v_ptr,
+                      std::vector<int32_t>& u_idx, std::vector<float>& w_t) {
+  v_ptr.assign(n_v + 1, 0);
+  u_idx.resize(nnz);
+  if (w) w_t.resize(nnz);
+  for (int64_t j = 0; j < nnz; ++j) v_ptr[v_idx[j] + 1]++;
+  for (int64_t c = 0; c < n_v; ++c) v_ptr[c + 1] += v_ptr[c];
+  std::vector<int64_t> cur(v_ptr.begin(), v_ptr.end() - 1);
+  for (int64_t r = 0; r < n_u; ++r)
+    for (int64_t j = u_ptr[r]; j < u_ptr[r + 1]; ++j) {
+      int64_t p = cur[v_idx[j]]++;
+      u_idx[p] = (int32_t)r;
+      if (w) w_t[p] = w[j];
+    }
+}
+
+// Row schedule of one SpMM direction: light rows by decreasing degree (coarse
+// log2 buckets, stable), heavy rows cut into kHeavyChunk-edge chunks.
+static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_graph::Schedule& sc,
+                          cudaStream_t s) {
+  std::vector<int32_t> light;
+  std::vector<int64_t> cb;
+  std::vector<int32_t> cslot;
+  std::vector<int32_t> hrow;
+  std::vector<int64_t> hc0;
+  light.reserve(rows);
+  std::vector<int64_t> bucket_count(64, 0);
+  auto bucket = [](int64_t deg) { return deg <= 0 ? 0 : 64 - __builtin_clzll((uint64_t)deg); };
+  for (int64_t r = 0; r < rows; ++r) {
+    int64_t deg = ptr[r + 1] - ptr[r];
+    if (deg > kHeavyRow) {
+      hc0.push_back((int64_t)cb.size());
+      int32_t slot = (int32_t)hrow.size();
+      hrow.push_back((int32_t)r);
+      for (int64_t b = ptr[r]; b < ptr[r + 1]; b += kHeavyChunk) {
+        cb.push_back(b);
+        cslot.push_back(slot);
+      }
+    } else {
+      bucket_count[bucket(deg)]++;
+    }
+  }
+  hc0.push_back((int64_t)cb.size());
+  // descending buckets
+  std::vector<int64_t> start(64, 0);
+  int64_t acc = 0;
+  for (int bk = 63; bk >= 0; --bk) {
+    start[bk] = acc;
+    acc += bucket_count[bk];
+  }
+  light.resize(acc);
+  for (int64_t r = 0; r < rows; ++r) {
+    int64_t deg = ptr[r + 1] - ptr[r];
+    if (deg <= kHeavyRow) light[start[bucket(deg)]++] = (int32_t)r;
+  }
+  sc.n_light = (int64_t)light.size();
+  sc.n_chunks = (int64_t)cb.size();
+  sc.n_heavy = (int64_t)hrow.size();
+  void* p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * std::max<int64_t>(1, sc.n_light), s));
+  sc.light = (int32_t*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int64_t) * std::max<int64_t>(1, sc.n_chunks), s));
+  sc.chunk_begin = (int64_t*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * std::max<int64_t>(1, sc.n_chunks), s));
+  sc.chunk_row_slot = (int32_t*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * std::max<int64_t>(1, sc.n_heavy), s));
+  sc.heavy_row = (int32_t*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int64_t) * (sc.n_heavy + 1), s));
+  sc.heavy_chunk0 = (int64_t*)p;
+  if (sc.n_light)
+    ABG_CUDA(cudaMemcpyAsync(sc.light, light.data(), sizeof(int32_t) * sc.n_light,
+                             cudaMemcpyHostToDevice, s));
+  if (sc.n_chunks) {
+    ABG_CUDA(cudaMemcpyAsync(sc.chunk_begin, cb.data(), sizeof(int64_t) * sc.n_chunks,
+                             cudaMemcpyHostToDevice, s));
+    ABG_CUDA(cudaMemcpyAsync(sc.chunk_row_slot, cslot.data(), sizeof(int32_t) * sc.n_chunks,
+                             cudaMemcpyHostToDevice, s));
+    ABG_CUDA(cudaMemcpyAsync(sc.heavy_row, hrow.data(), sizeof(int32_t) * sc.n_heavy,
+                             cudaMemcpyHostToDevice, s));
+  }
+  ABG_CUDA(cudaMemcpyAsync(sc.heavy_chunk0, hc0.data(), sizeof(int64_t) * (sc.n_heavy + 1),
+                           cudaMemcpyHostToDevice, s));
+  // the host vectors must outlive the copies
+  ABG_CUDA(cudaStreamSynchronize(s));
+  return ABG_OK;
+}
+
+template <class T>
+static int upload(abg_graph* g, T** dst, const T* src, int64_t count, cudaStream_t s) {
+  void* p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(T) * std::max<int64_t>(1, count), s));
+  *dst = (T*)p;
+  if (count) ABG_CUDA(cudaMemcpyAsync(p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  return ABG_OK;
+}
+
+static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
+  ABG_CHECK(d, "null descriptor");
+  ABG_CHECK(d->n_u >= 1 && d->n_v >= 1 && d->n_u < (1ll << 31) && d->n_v < (1ll << 31),
+            "need 1 <= |U|, |V| < 2^31");
+  ABG_CHECK(d->nnz >= 0, "nnz < 0");
+  ABG_CHECK(d->d_u >= 1 && d->d_u <= 65536, "need 1 <= d_u <= 65536");
+  ABG_CHECK(d->x_kind >= ABG_X_DENSE_F32 && d->x_kind <= ABG_X_CSR_F32, "bad x_kind");
+  g->device = d->device;
+  g->n_u = d->n_u;
+  g->n_v = d->n_v;
+  g->nnz = d->nnz;
+  g->d_u = d->d_u;
+  g->x_kind = d->x_kind;
+  ABG_TRY(validate_csr(d->u_ptr, d->v_idx, d->w, d->n_u, d->n_v, d->nnz, "CSR"));
+  const bool have_csc = d->v_ptr || d->u_idx || d->w_t;
+  std::vector<int64_t> vp;
+  std::vector<int32_t> ui;
+  std::vector<float> wt;
+  const int64_t* v_ptr = d->v_ptr;
+  const int32_t* u_idx = d->u_idx;
+  const float* w_t = d->w_t;
+  if (have_csc) {
+    ABG_CHECK(d->v_ptr && d->u_idx && (!d->w == !d->w_t),
+              "CSC needs v_ptr, u_idx and (w_t iff w)");
+    ABG_TRY(validate_csr(d->v_ptr, d->u_idx, d->w_t, d->n_v, d->n_u, d->nnz, "CSC"));
+  } else {
+    build_csc(d->n_u, d->n_v, d->nnz, d->u_ptr, d->v_idx, d->w, vp, ui, wt);
+    v_ptr = vp.data();
+    u_idx = ui.data();
+    w_t = d->w ? wt.data() : nullptr;
+  }
+  // attributes
+  if (d->x_kind == ABG_X_CSR_F32) {
+    ABG_TRY(validate_csr(d->x_ptr, d->x_idx, nullptr, d->n_u, d->d_u, d->x_ptr ? d->x_ptr[d->n_u] : 0,
+                         "X CSR"));
+    ABG_CHECK(d->x_val, "X CSR: null values");
+    g->x_nnz = d->x_ptr[d->n_u];
+    for (int64_t j = 0; j < g->x_nnz; ++j)
+      ABG_CHECK(std::isfinite(d->x_val[j]), "X CSR: non-finite value at %lld", (long long)j);
+  } else {
+    ABG_CHECK(d->x, "dense attributes: null x");
+  }
+
+  // ---- upload + device work (all validation above is host-only) ----
+  ABG_CUDA(cudaSetDevice(d->device));
+  ABG_TRY(upload(g, &g->u_ptr, d->u_ptr, d->n_u + 1, s));
+  ABG_TRY(upload(g, &g->u_col, d->v_idx, d->nnz, s));
+  ABG_TRY(upload(g, &g->v_ptr, v_ptr, d->n_v + 1, s));
+  ABG_TRY(upload(g, &g->v_col, u_idx, d->nnz, s));
+  float *w_dev = nullptr, *wt_dev = nullptr;
+  Scratch scr(s);
+  if (d->w) {
+    ABG_TRY(scr.get(&w_dev, d->nnz));
+    ABG_TRY(scr.get(&wt_dev, d->nnz));
+    ABG_CUDA(cudaMemcpyAsync(w_dev, d->w, sizeof(float) * d->nnz, cudaMemcpyHostToDevice, s));
+    ABG_CUDA(cudaMemcpyAsync(wt_dev, w_t, sizeof(float) * d->nnz, cudaMemcpyHostToDevice, s));
+  }
+  void* p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(float) * std::max<int64_t>(1, d->nnz), s));
+  g->u_val = (float*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(float) * std::max<int64_t>(1, d->nnz), s));
+  g->v_val = (float*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(float) * d->n_u, s));
+  g->su = (float*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(float) * d->n_v, s));
+  g->sv = (float*)p;
+  if (have_csc) {  // the CSC must hold the CSR's edges: equal per-column counts
+    int *cnt, *bad;
+    ABG_TRY(scr.get(&cnt, d->n_v));
+    ABG_TRY(scr.get(&bad, 1));
+    ABG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * d->n_v, s));
+    ABG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (d->nnz) { k_col_count<<<num_sms() * 8, 256, 0, s>>>(g->u_col, d->nnz, cnt); ::abg::note_launch(); }
+    k_count_mismatch<<<num_sms() * 4, 256, 0, s>>>(g->v_ptr, cnt, d->n_v, bad); ::abg::note_launch();
+    ABG_LAUNCH_CHECK();
+    int hbad = 0;
+    ABG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaStreamSynchronize(s));
+    ABG_CHECK(hbad == 0, "CSC does not match the CSR (%d columns differ)", hbad);
+  }
+  const int wpb = 8;
+  k_row_scale<<<ceil_div(d->n_u, wpb), wpb * 32, 0, s>>>(g->u_ptr, w_dev, d->n_u, g->su); ::abg::note_launch();
+  k_row_scale<<<ceil_div(d->n_v, wpb), wpb * 32, 0, s>>>(g->v_ptr, wt_dev, d->n_v, g->sv); ::abg::note_launch();
+  k_l_values<<<ceil_div(d->n_u, wpb), wpb * 32, 0, s>>>(g->u_ptr, g->u_col, w_dev, d->n_u, g->su,
+                                                        g->sv, g->u_val); ::abg::note_launch();
+  k_l_values<<<ceil_div(d->n_v, wpb), wpb * 32, 0, s>>>(g->v_ptr, g->v_col, wt_dev, d->n_v, g->sv,
+                                                        g->su, g->v_val); ::abg::note_launch();
+  ABG_LAUNCH_CHECK();
+
+  // attributes on the device
+  if (d->x_kind == ABG_X_DENSE_F32 || d->x_kind == ABG_X_DENSE_BF16) {
+    const int esz = d->x_kind == ABG_X_DENSE_F32 ? 4 : 2;
+    g->ldx = round_up(d->d_u, 8);
+    ABG_TRY(graph_alloc(g, &p, (size_t)esz * g->ldx * d->n_u, s));
+    g->x = p;
+    ABG_CUDA(cudaMemcpy2DAsync(p, (size_t)esz * g->ldx, d->x, (size_t)esz * d->d_u,
+                               (size_t)esz * d->d_u, d->n_u, cudaMemcpyHostToDevice, s));
+    if (g->ldx != d->d_u)
+      ABG_CUDA(cudaMemset2DAsync((char*)p + (size_t)esz * d->d_u, (size_t)esz * g->ldx, 0,
+                                 (size_t)esz * (g->ldx - d->d_u), d->n_u, s));
+  } else {
+    ABG_TRY(upload(g, &g->x_ptr, d->x_ptr, d->n_u + 1, s));
+    ABG_TRY(upload(g, &g->x_col, d->x_idx, g->x_nnz, s));
+    ABG_TRY(upload(g, &g->x_val, d->x_val, g->x_nnz, s));
+    std::vector<int64_t> tp;
+    std::vector<int32_t> ti;
+    std::vector<float> tv;
+    build_csc(d->n_u, d->d_u, g->x_nnz, d->x_ptr, d->x_idx, d->x_val, tp, ti, tv);
+    ABG_TRY(upload(g, &g->xt_ptr, tp.data(), d->d_u + 1, s));
+    ABG_TRY(upload(g, &g->xt_col, ti.data(), g->x_nnz, s));
+    ABG_TRY(upload(g, &g->xt_val, tv.data(), g->x_nnz, s));
+    ABG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+  }
+  ABG_TRY(build_schedule(g, d->u_ptr, d->n_u, g->sched_u, s));
+  ABG_TRY(build_schedule(g, v_ptr, d->n_v, g->sched_v, s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  return ABG_OK;
+}
+
+extern "C" {
+
+ABG_API const char* abg_strerror(int st) {
+  switch (st) {
+    case ABG_OK: return "ok";
+    case ABG_PENDING: return "pending";
+    case ABG_EINVAL: return "invalid argument";
+    case ABG_ENOMEM: return "out of device memory";
+    case ABG_EDEVICE: return "CUDA device error";
+    case ABG_ENOTADMITTED: return "job does not fit the server's memory budget";
+    case ABG_ETIMEDOUT: return "timed out";
+    case ABG_ENOTFOUND: return "unknown request";
+    case ABG_ECANCELLED: return "cancelled";
+    case ABG_ENUMERIC: return "numerical failure";
+    default: return "unknown status";
+  }
+}
+
+ABG_API const char* abg_last_error(void) { return g_err; }
+
+ABG_API int64_t abg_launch_count(void) { return g_launches.load(); }
+
+ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out) {
+  if (!out) {
+    set_error("null output pointer");
+    return ABG_EINVAL;
+  }
+  *out = nullptr;
+  abg_graph* g = new abg_graph();
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = create_impl(desc, s, g);
+  if (st != ABG_OK) {
+    abg_destroy(g);
+    return st;
+  }
+  *out = g;
+  return ABG_OK;
+}
+
+ABG_API void abg_destroy(abg_graph* g) {
+  if (!g) return;
+  if (g->n_blocks) {
+    cudaSetDevice(g->device);
+    for (int i = 0; i < g->n_blocks; ++i) cudaFreeAsync(g->blocks[i], 0);
+    cudaStreamSynchronize(0);
+  }
+  delete g;
+}
+
+ABG_API int64_t abg_graph_footprint(const abg_graph* g) { return g ? g->footprint : 0; }
+
+}  // extern "C"
