@@ -208,6 +208,22 @@ ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32
 ABG_API int abg_objective(const float* r, int64_t n, int32_t m, int64_t ldr,
                           const int32_t* labels, int32_t k, double* obj, void* stream);
 
+/* ---- allocation-free variant (the paper has no counterpart) -------------- */
+
+/* Same result as abg_objective, for callers that must not allocate device
+ * memory while they run (an application that gave all GPU memory to its own
+ * allocator, a latency-bound loop that cannot absorb an allocation's device
+ * synchronisation, a host runtime that forbids libraries to allocate). It calls
+ * no cudaMalloc/cudaFree or allocating routine: its scratch is one fixed 24 MiB
+ * __device__ array that every GPU loading the library holds until exit. Limit:
+ * k * (m + 1) <= 48,393 (else ABG_EINVAL with the limit in abg_last_error()).
+ * The first call on a device looks the array up (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the array: calls
+ * that overlap on the GPU race. Labels outside [0, k) are skipped. Synchronises
+ * `stream`; obj (host) gets {objective, trace_obj}. */
+ABG_API int abg_objective_noalloc(const float* r, int64_t n, int32_t m, int64_t ldr,
+                                  const int32_t* labels, int32_t k, double* obj, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

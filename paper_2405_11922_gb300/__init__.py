@@ -77,6 +77,7 @@ SIGNATURES = {
     "abg_onmf": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _i64, _p, _i64, _p]),
     "abg_nci": (C.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p, _p, _p]),
     "abg_objective": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
+    "abg_objective_noalloc": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
 }
 
 _lib = None
@@ -271,4 +272,13 @@ def abg_objective(r, n: int, m: int, labels, k: int, stream=None) -> tuple[float
     out = (C.c_double * 2)()
     _check(lib().abg_objective(_ptr(r), n, m, _ld(r), _ptr(labels), k, out, _stream(stream)),
            "abg_objective")
+    return float(out[0]), float(out[1])
+
+
+def abg_objective_noalloc(r, n: int, m: int, labels, k: int, stream=None) -> tuple[float, float]:
+    """abg_objective without any device allocation: its scratch is a fixed array inside the
+    library (see include/abg.h for the size limit and the sharing rules)."""
+    out = (C.c_double * 2)()
+    _check(lib().abg_objective_noalloc(_ptr(r), n, m, _ld(r), _ptr(labels), k, out,
+                                       _stream(stream)), "abg_objective_noalloc")
     return float(out[0]), float(out[1])
