@@ -29,14 +29,38 @@ struct EpiNN {
   // random features (mode 5): scale inside sin/cos, factor outside, width d, partial colsums
   float in_scale, out_scale;
   double* colsum_part;  // [gridDim.x][2N]
+  // NCI scores (mode 6): row argmax over the N columns (ties -> lowest column), top1 - top2
+  int32_t* labels;
+  float* margin;
+  int first;
+  int* changes;
+  unsigned* min_margin_bits;
 };
 constexpr int kEpiSinCos = 5;
+constexpr int kEpiArgmax = 6;
+
+struct Best {
+  float v;
+  int i;
+  float s;
+};
+__device__ __forceinline__ Best merge_best(Best a, Best b) {
+  Best r;
+  if (a.v > b.v || (a.v == b.v && a.i < b.i)) {
+    r = a;
+    r.s = fmaxf(a.s, b.v);
+  } else {
+    r = b;
+    r.s = fmaxf(b.s, a.v);
+  }
+  return r;
+}
 
 // ---------------------------------------------------------------------------
 // C = A (M x K) * B (K x N), CTA tile 128 x (16*TN), K step 16, 256 threads,
 // thread tile 8 rows x TN columns (columns (tx + 16 j) * 4 .. +4 for TN >= 4).
 // ---------------------------------------------------------------------------
-template <int TN, bool SC>
+template <int TN, int EPI>  // EPI: 0 element-wise, 1 sin/cos + column sums, 2 row argmax
 __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int N, int K,
                                                  const float* __restrict__ A, int64_t lda,
                                                  const float* __restrict__ B, int64_t ldb,
@@ -121,7 +145,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int N, int K,
   auto col_of = [&](int j) -> int {
     return TN >= 4 ? n0 + (tx + 16 * (j / 4)) * 4 + (j & 3) : n0 + tx * TN + j;
   };
-  if constexpr (SC) {
+  if constexpr (EPI == 1) {
     // R'[i, n] = out_scale * sin(in_scale * acc), R'[i, N + n] = out_scale * cos(...);
     // per-CTA column sums of R' (FP64, fixed order over the 16 row groups)
     __shared__ double csum[16][2 * BN];
@@ -160,6 +184,44 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int N, int K,
       const int gn = n0 + cl;
       if (gn < N) ep.colsum_part[(int64_t)blockIdx.x * 2 * N + (c < BN ? gn : N + gn)] = s;
     }
+  } else if constexpr (EPI == 2) {
+    // Eq. 21: l* = argmax_l (Phi T)[i, l]; the row's columns live on the 16 lanes of equal ty
+    // (one grid column covers all N <= 16*TN columns); reduce with shuffles inside 16 lanes
+    int old_lab[TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gm = m0 + ty * TM + i;
+      old_lab[i] = (!ep.first && tx == 0 && gm < M) ? ep.labels[gm] : -1;
+    }
+    int local_changes = 0;
+    float local_min = INFINITY;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      Best b{-INFINITY, 0x7fffffff, -INFINITY};
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int gn = col_of(j);
+        if (gn < N) b = merge_best(b, Best{acc[i][j], gn, -INFINITY});
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        Best other;
+        other.v = __shfl_xor_sync(0xffffffffu, b.v, o);
+        other.i = __shfl_xor_sync(0xffffffffu, b.i, o);
+        other.s = __shfl_xor_sync(0xffffffffu, b.s, o);
+        b = merge_best(b, other);
+      }
+      const int64_t gm = m0 + ty * TM + i;
+      if (tx == 0 && gm < M) {
+        const float mg = N > 1 ? b.v - b.s : INFINITY;
+        if (!ep.first && old_lab[i] != b.i) ++local_changes;
+        ep.labels[gm] = b.i;
+        if (ep.margin) ep.margin[gm] = mg;
+        local_min = fminf(local_min, mg);
+      }
+    }
+    if (local_changes) atomicAdd(ep.changes, local_changes);
+    if (local_min < INFINITY) atomicMin(ep.min_margin_bits, __float_as_uint(fmaxf(local_min, 0.f)));
   } else {
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -193,9 +255,11 @@ static void launch_nn(int64_t M, int N, int K, const float* A, int64_t lda, cons
                       int64_t ldb, float* C, int64_t ldc, const EpiNN& ep, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(M, 128), (unsigned)ceil_div(N, 16 * TN));
   if (ep.mode == kEpiSinCos) {
-    k_gemm_nn<TN, true><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, ep); ::abg::note_launch();
+    k_gemm_nn<TN, 1><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, ep); ::abg::note_launch();
+  } else if (ep.mode == kEpiArgmax) {
+    k_gemm_nn<TN, 2><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, ep); ::abg::note_launch();
   } else {
-    k_gemm_nn<TN, false><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, ep); ::abg::note_launch();
+    k_gemm_nn<TN, 0><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, ep); ::abg::note_launch();
   }
 }
 
@@ -470,100 +534,6 @@ int nmf_update_h(int m, int k, float* H, int64_t ldh, const double* A, int64_t l
 // ---------------------------------------------------------------------------
 // Algorithm 3: NCI generation
 // ---------------------------------------------------------------------------
-// Scores Phi[i] . T[:, l] for a tile of rows, argmax with ties to the lowest l,
-// margin top1 - top2; persistent CTAs keep T in shared memory. TPR threads per
-// row group, each thread 4 rows x 4 columns.
-struct Best {
-  float v;
-  int i;
-  float s;
-};
-__device__ __forceinline__ Best merge_best(Best a, Best b) {
-  Best r;
-  if (a.v > b.v || (a.v == b.v && a.i < b.i)) {
-    r = a;
-    r.s = fmaxf(a.s, b.v);
-  } else {
-    r = b;
-    r.s = fmaxf(b.s, a.v);
-  }
-  return r;
-}
-
-template <int TPR>
-__global__ void __launch_bounds__(256) k_nci_scores(int64_t n, int k, const float* __restrict__ phi,
-                                                    int64_t ldphi, const float* __restrict__ T,
-                                                    int kp, int32_t* __restrict__ labels,
-                                                    float* __restrict__ margin, int first,
-                                                    int* __restrict__ changes,
-                                                    unsigned* __restrict__ min_margin_bits) {
-  constexpr int RG = 256 / TPR;      // row groups per CTA
-  constexpr int ROWS = 4 * RG;       // rows per tile
-  extern __shared__ __align__(16) float sm[];
-  float* Ts = sm;                    // [k][kp]
-  float* Ps = sm + k * kp;           // [k][ROWS] (transposed tile)
-  const int tid = threadIdx.x;
-  const int c = tid % TPR, rg = tid / TPR;
-  for (int q = tid; q < k * kp; q += 256) Ts[q] = T[q];
-  int local_changes = 0;
-  float local_min = INFINITY;
-  const int64_t ntiles = ceil_div(n, ROWS);
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * ROWS;
-    __syncthreads();
-    for (int q = tid; q < ROWS * k; q += 256) {
-      const int rr = q / k, m = q % k;
-      const int64_t gr = r0 + rr;
-      Ps[m * ROWS + rr] = gr < n ? phi[gr * ldphi + m] : 0.f;
-    }
-    __syncthreads();
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    if (c * 4 < k) {
-      for (int m = 0; m < k; ++m) {
-        const float4 pv = *reinterpret_cast<const float4*>(&Ps[m * ROWS + rg * 4]);
-        const float4 tv = *reinterpret_cast<const float4*>(&Ts[m * kp + c * 4]);
-        const float p[4] = {pv.x, pv.y, pv.z, pv.w};
-        const float t[4] = {tv.x, tv.y, tv.z, tv.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(p[i], t[j], acc[i][j]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      Best b{-INFINITY, 0x7fffffff, -INFINITY};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int l = c * 4 + j;
-        if (l < k) b = merge_best(b, Best{acc[i][j], l, -INFINITY});
-      }
-#pragma unroll
-      for (int o = TPR / 2; o > 0; o >>= 1) {
-        Best other;
-        other.v = __shfl_xor_sync(0xffffffffu, b.v, o, TPR);
-        other.i = __shfl_xor_sync(0xffffffffu, b.i, o, TPR);
-        other.s = __shfl_xor_sync(0xffffffffu, b.s, o, TPR);
-        b = merge_best(b, other);
-      }
-      const int64_t gr = r0 + rg * 4 + i;
-      if (c == 0 && gr < n) {
-        const float mg = k > 1 ? b.v - b.s : INFINITY;
-        if (!first && labels[gr] != b.i) ++local_changes;
-        labels[gr] = b.i;
-        if (margin) margin[gr] = mg;
-        local_min = fminf(local_min, mg);
-      }
-    }
-  }
-  if (local_changes) atomicAdd(changes, local_changes);
-  if (local_min < INFINITY) atomicMin(min_margin_bits, __float_as_uint(fmaxf(local_min, 0.f)));
-}
-
 // Per-chunk cluster sums S[l][m] = sum_{i in chunk, label i = l} Phi[i, m] and counts; one
 // thread per column, rows in order (deterministic).
 __global__ void k_cluster_sums(int64_t n, int k, int w, const float* __restrict__ X, int64_t ldx,
@@ -578,10 +548,30 @@ __global__ void k_cluster_sums(int64_t n, int k, int w, const float* __restrict_
   const int m = threadIdx.x;
   const int gm = col0 + m;
   const bool active = m < wtile && gm < w;
-  for (int64_t r = r0; r < r1; ++r) {
+  const bool counter = threadIdx.x == 0 && blockIdx.y == 0;
+  // 8 rows of loads in flight per thread, then the ordered shared-memory adds
+  constexpr int U = 8;
+  int64_t r = r0;
+  for (; r + U <= r1; r += U) {
+    int l[U];
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      l[u] = labels[r + u];
+      v[u] = active ? X[(r + u) * ldx + gm] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if ((unsigned)l[u] >= (unsigned)k) continue;  // labels outside [0, k) are skipped
+      if (active) accs[l[u] * wtile + m] += v[u];
+      if (counter) cnt[l[u]] += 1.f;
+    }
+  }
+  for (; r < r1; ++r) {
     const int l = labels[r];
+    if ((unsigned)l >= (unsigned)k) continue;
     if (active) accs[l * wtile + m] += X[r * ldx + gm];
-    if (threadIdx.x == 0 && blockIdx.y == 0) cnt[l] += 1.f;
+    if (counter) cnt[l] += 1.f;
   }
   __syncthreads();
   // partial layout per chunk: [k][w] sums then [k] counts
@@ -659,30 +649,10 @@ int nci_run(const float* phi, int64_t n, int k, int64_t ldphi, int t_g, int32_t*
   int* counters;  // [0] changes, [1] min margin bits, [2] empty clusters
   ABG_TRY(scr.get(&counters, 4));
   k_identity<<<(unsigned)ceil_div(k * kp, 256), 256, 0, s>>>(k, kp, T); ::abg::note_launch();
-  int tpr = 1;
-  while (tpr * 4 < k) tpr *= 2;
-  const int rows_per_tile = 4 * (256 / tpr);
-  const size_t smem = sizeof(float) * ((size_t)k * kp + (size_t)k * rows_per_tile);
-  const int64_t ntiles = ceil_div(n, rows_per_tile);
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, num_sms() * 2));
   auto launch_scores = [&](int first) -> int {
-#define ABG_NCI_CASE(tp)                                                                        \
-  if (tpr == tp) {                                                                              \
-    if (smem > 48 * 1024)                                                                       \
-      ABG_CUDA(cudaFuncSetAttribute(k_nci_scores<tp>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    (int)smem));                                                \
-    k_nci_scores<tp><<<grid, 256, smem, s>>>(n, k, phi, ldphi, T, kp, labels, margin, first,    \
-                                             counters, (unsigned*)(counters + 1)); ::abg::note_launch();              \
-  }
-    ABG_NCI_CASE(1)
-    ABG_NCI_CASE(2)
-    ABG_NCI_CASE(4)
-    ABG_NCI_CASE(8)
-    ABG_NCI_CASE(16)
-    ABG_NCI_CASE(32)
-#undef ABG_NCI_CASE
-    ABG_LAUNCH_CHECK();
-    return ABG_OK;
+    EpiNN ep{kEpiArgmax, nullptr, 0, nullptr, 0, nullptr, 1.f, 1.f, nullptr,
+             labels, margin, first, counters, (unsigned*)(counters + 1)};
+    return gemm_nn_impl(n, k, k, phi, ldphi, T, kp, nullptr, 0, ep, s);
   };
   for (int t = 0; t < t_g; ++t) {
     k_reset_counters<<<1, 1, 0, s>>>(counters); ::abg::note_launch();

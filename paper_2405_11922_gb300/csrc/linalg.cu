@@ -89,13 +89,16 @@ int gaussian_f32(uint64_t seed, int stream_id, int rows, int cols, float* out, i
 // work: l*l doubles (R), rinv64: l*l doubles; rinv32 (optional): l x ldr floats.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restrict__ G, int64_t ldg,
-                                                   double* __restrict__ R, double* __restrict__ Ri,
+                                                   double* __restrict__ Rg, double* __restrict__ Rig,
                                                    float* __restrict__ ri32, int64_t ldr32,
-                                                   int* __restrict__ breakdowns) {
+                                                   int* __restrict__ breakdowns, int in_smem) {
+  extern __shared__ double csm[];
+  double* R = in_smem ? csm : Rg;                    // l x l, upper triangle used
+  double* Ri = in_smem ? csm + (int64_t)l * l : Rig; // l x l
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
   __shared__ double s_piv;
   __shared__ double s_maxdiag;
-  // copy upper triangle
   for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
     const int i = (int)(q / l), j = (int)(q % l);
     R[q] = j >= i ? G[(int64_t)i * ldg + j] : 0.0;
@@ -125,17 +128,14 @@ __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restri
       R[(int64_t)j * l + c] = piv > 0.0 ? (c == j ? piv : v / piv) : 0.0;
     }
     __syncthreads();
-    // trailing update A[r][c] -= R[j][r] R[j][c], j < r <= c
-    const int n = l - j - 1;
-    const int64_t cnt = (int64_t)n * n;
-    for (int64_t q = tid; q < cnt; q += nt) {
-      const int r = j + 1 + (int)(q / n), c = j + 1 + (int)(q % n);
-      if (c >= r) R[(int64_t)r * l + c] -= R[(int64_t)j * l + r] * R[(int64_t)j * l + c];
+    // trailing update A[r][c] -= R[j][r] R[j][c] for j < r <= c: a warp per row
+    for (int r = j + 1 + warp; r < l; r += nw) {
+      const double rjr = R[(int64_t)j * l + r];
+      for (int c = r + lane; c < l; c += 32) R[(int64_t)r * l + c] -= rjr * R[(int64_t)j * l + c];
     }
     __syncthreads();
   }
   // inverse of the upper-triangular R, one warp per column (back substitution)
-  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
   for (int j = warp; j < l; j += nw) {
     for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
     __syncwarp();
@@ -151,14 +151,31 @@ __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restri
       }
       __syncwarp();
     }
-    // a dropped pivot anywhere on the diagonal of this column's block zeroes the column
+    // a dropped pivot on the diagonal zeroes this column of R^-1
     if (R[(int64_t)j * l + j] <= 0.0)
       for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
   }
   __syncthreads();
-  if (ri32)
-    for (int64_t q = tid; q < (int64_t)l * l; q += nt)
-      ri32[(q / l) * ldr32 + (q % l)] = (float)Ri[q];
+  for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
+    const double v = Ri[q];
+    if (in_smem) Rig[q] = v;
+    if (ri32) ri32[(q / l) * ldr32 + (q % l)] = (float)v;
+  }
+}
+
+// Launch k_chol_inv with both triangles in shared memory when they fit.
+static int chol_inv(int l, const double* G, int64_t ldg, double* R, double* Ri, float* ri32,
+                    int64_t ldr32, int* breakdowns, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 2 * (size_t)l * l;
+  const int in_smem = smem <= 200 * 1024;
+  if (in_smem)
+    ABG_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  k_chol_inv<<<1, 1024, in_smem ? smem : 0, s>>>(l, G, ldg, R, Ri, ri32, ldr32, breakdowns,
+                                                 in_smem);
+  ::abg::note_launch();
+  ABG_LAUNCH_CHECK();
+  return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +272,7 @@ int orthogonal_matrix(uint64_t seed, int d, double* q, cudaStream_t s) {
   double* dst = T;
   for (int pass = 0; pass < 2; ++pass) {
     small_tn64(d, d, d, src, d, src, d, Gram, d, s);
-    k_chol_inv<<<1, 1024, 0, s>>>(d, Gram, d, R, Ri, nullptr, 0, bd); ::abg::note_launch();
+    ABG_TRY(chol_inv(d, Gram, d, R, Ri, nullptr, 0, bd, s));
     small_nn64(d, d, d, src, d, Ri, d, pass == 1 ? q : dst, d, s);
     src = dst;
   }
@@ -283,8 +300,7 @@ int cholqr2(int64_t M, int l, float* Y, int64_t ldy, float* tmp, int64_t ldt, in
     float* dst = pass == 0 ? tmp : Y;
     const int64_t ldd = pass == 0 ? ldt : ldy;
     ABG_TRY(gemm_tn(M, l, l, src, lds, src, lds, Gram, l, scr, s));
-    k_chol_inv<<<1, 1024, 0, s>>>(l, Gram, l, R, Ri, ri32, ll, breakdowns); ::abg::note_launch();
-    ABG_LAUNCH_CHECK();
+    ABG_TRY(chol_inv(l, Gram, l, R, Ri, ri32, ll, breakdowns, s));
     ABG_TRY(gemm_nn(M, l, l, src, lds, ri32, ll, dst, ldd, Epi::Store, nullptr, 0, nullptr, 0,
                     nullptr, s));
   }
@@ -296,10 +312,11 @@ int cholqr2(int64_t M, int l, float* Y, int64_t ldy, float* tmp, int64_t ldt, in
 // robin pairing so the l/2 rotations of a step touch disjoint index pairs).
 // A is destroyed; evals (descending) and evecs (columns, l x l) are written.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ A, double* __restrict__ V,
+__global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ Ag, double* __restrict__ Vg,
                                                  double* __restrict__ evals,
-                                                 double* __restrict__ evecs, int max_sweeps) {
-  extern __shared__ double js[];  // cs[m/2], sn[m/2], pp[m/2], qq[m/2] (as double), diag[l], red
+                                                 double* __restrict__ evecs, int max_sweeps,
+                                                 int a_smem, int v_smem) {
+  extern __shared__ double js[];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = (l + 1) & ~1;  // even player count (index l is a dummy when l is odd)
   const int P = m / 2;
@@ -307,11 +324,15 @@ __global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ A, 
   double* sn = js + P;
   int* pp = reinterpret_cast<int*>(js + 2 * P);
   int* qq = pp + P;
-  double* red = js + 3 * P + 1;
+  double* red = js + 3 * P + 1;             // 2 * nt + 1
+  double* tail = red + 2 * nt + 2;
+  double* A = a_smem ? tail : Ag;
+  double* V = v_smem ? tail + (a_smem ? (int64_t)l * l : 0) : Vg;
+  if (a_smem)
+    for (int64_t q = tid; q < (int64_t)l * l; q += nt) A[q] = Ag[q];
   for (int64_t q = tid; q < (int64_t)l * l; q += nt) V[q] = ((q / l) == (q % l)) ? 1.0 : 0.0;
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal energy vs total
     double off = 0.0, tot = 0.0;
     for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
       const double v = A[q] * A[q];
@@ -333,12 +354,11 @@ __global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ A, 
     if (red[2 * nt] != 0.0) break;
     __syncthreads();
     for (int step = 0; step < m - 1; ++step) {
-      // pairs of this step: player 0 fixed, players 1..m-1 rotate
       for (int i = tid; i < P; i += nt) {
         auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (m - 1)) + 1; };
         int a = player(i), b = player(m - 1 - i);
         int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
+        double c = 1.0, sv = 0.0;
         if (q < l) {
           const double apq = A[(int64_t)p * l + q];
           if (apq != 0.0) {
@@ -346,38 +366,41 @@ __global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ A, 
             const double theta = (aqq - app) / (2.0 * apq);
             const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
+            sv = t * c;
           }
         }
         cs[i] = c;
-        sn[i] = s;
+        sn[i] = sv;
         pp[i] = p;
         qq[i] = q;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int64_t w = tid; w < (int64_t)P * l; w += nt) {
-        const int i = (int)(w / l), k = (int)(w % l);
+      // rows: A <- J^T A (a warp per pair, lanes over columns)
+      const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
+      for (int i = warp; i < P; i += nw) {
         const int p = pp[i], q = qq[i];
         if (q >= l) continue;
-        const double c = cs[i], s = sn[i];
-        const double apk = A[(int64_t)p * l + k], aqk = A[(int64_t)q * l + k];
-        A[(int64_t)p * l + k] = c * apk - s * aqk;
-        A[(int64_t)q * l + k] = s * apk + c * aqk;
+        const double c = cs[i], sv = sn[i];
+        for (int k = lane; k < l; k += 32) {
+          const double apk = A[(int64_t)p * l + k], aqk = A[(int64_t)q * l + k];
+          A[(int64_t)p * l + k] = c * apk - sv * aqk;
+          A[(int64_t)q * l + k] = sv * apk + c * aqk;
+        }
       }
       __syncthreads();
       // columns: A <- A J, V <- V J
-      for (int64_t w = tid; w < (int64_t)P * l; w += nt) {
-        const int i = (int)(w / l), k = (int)(w % l);
+      for (int i = warp; i < P; i += nw) {
         const int p = pp[i], q = qq[i];
         if (q >= l) continue;
-        const double c = cs[i], s = sn[i];
-        const double akp = A[(int64_t)k * l + p], akq = A[(int64_t)k * l + q];
-        A[(int64_t)k * l + p] = c * akp - s * akq;
-        A[(int64_t)k * l + q] = s * akp + c * akq;
-        const double vkp = V[(int64_t)k * l + p], vkq = V[(int64_t)k * l + q];
-        V[(int64_t)k * l + p] = c * vkp - s * vkq;
-        V[(int64_t)k * l + q] = s * vkp + c * vkq;
+        const double c = cs[i], sv = sn[i];
+        for (int k = lane; k < l; k += 32) {
+          const double akp = A[(int64_t)k * l + p], akq = A[(int64_t)k * l + q];
+          A[(int64_t)k * l + p] = c * akp - sv * akq;
+          A[(int64_t)k * l + q] = sv * akp + c * akq;
+          const double vkp = V[(int64_t)k * l + p], vkq = V[(int64_t)k * l + q];
+          V[(int64_t)k * l + p] = c * vkp - sv * vkq;
+          V[(int64_t)k * l + q] = sv * vkp + c * vkq;
+        }
       }
       __syncthreads();
     }
@@ -401,10 +424,16 @@ static int jacobi_eig(int l, double* A, double* evals, double* evecs, Scratch& /
   ABG_TRY(scr.get(&V, (size_t)l * l));
   const int threads = 1024;
   const int P = ((l + 1) & ~1) / 2;
-  const size_t smem = sizeof(double) * (3 * P + 1 + 2 * threads + 1);
+  const size_t base = sizeof(double) * (3 * P + 1 + 2 * threads + 2);
+  const size_t mat = sizeof(double) * (size_t)l * l;
+  const size_t limit = 220 * 1024;
+  const int a_smem = base + mat <= limit;
+  const int v_smem = a_smem && base + 2 * mat <= limit;
+  const size_t smem = base + (a_smem ? mat : 0) + (v_smem ? mat : 0);
   if (smem > 48 * 1024)
     ABG_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_jacobi<<<1, threads, smem, s>>>(l, A, V, evals, evecs, 40); ::abg::note_launch();
+  k_jacobi<<<1, threads, smem, s>>>(l, A, V, evals, evecs, 40, a_smem, v_smem);
+  ::abg::note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
