@@ -152,6 +152,61 @@ ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p); /*
 ABG_API int abg_cluster(abg_graph* g, const abg_params* p, void* stream, int32_t* labels,
                         abg_result* res);
 
+/* ---- many graphs per launch ---------------------------------------------- */
+
+/* Stack n graphs (host descriptors as for abg_create; same d_u and x_kind)
+ * into one block-diagonal graph whose n segments are solved together: one
+ * launch of each kernel serves every graph, and each graph's arithmetic is
+ * independent of the others (fixed-size tiles and chunks per graph), so its
+ * result is the same alone and in a batch. Segment s owns rows
+ * [sum_{t<s} n_u(t), +n_u(s)) of the stacked U. Free with abg_destroy. */
+ABG_API int abg_batch_create(const abg_graph_desc* descs, int32_t n, int32_t device, void* stream,
+                             abg_graph** out);
+ABG_API int32_t abg_graph_segments(const abg_graph* g);   /* 1 for abg_create graphs */
+
+/* Algorithms 1-3 for every segment: params[n] (k and seed may differ per
+ * graph; d, alpha, gamma, t_f, t_g, oversample, power_iters must agree),
+ * labels (host or device) for all stacked rows, results[n] (host, may be
+ * NULL). Synchronises `stream`. */
+ABG_API int abg_batch_cluster(abg_graph* batch, const abg_params* params, void* stream,
+                              int32_t* labels, abg_result* results);
+
+/* ---- request loop with continuous batching ------------------------------ */
+
+typedef struct abg_server abg_server;
+typedef struct {
+  int32_t device;
+  int32_t workers;            /* batches in flight at once, one CUDA stream each (default 3) */
+  int64_t hbm_budget_bytes;   /* admission: estimated device bytes of requests in flight */
+  int32_t max_batch_graphs;   /* requests stacked into one batched launch (default 64) */
+  int32_t batch_window_us;    /* a free worker waits this long for more requests (default 0) */
+  int64_t max_batch_rows;     /* U rows per batch (default 4M; one larger request runs alone) */
+} abg_server_opts;
+typedef struct {
+  int64_t submitted, completed, failed, rejected, batches, max_batch, pending, inflight_bytes;
+  int64_t latency_us_last;    /* submit -> completion of the last polled request */
+} abg_server_stats;
+
+ABG_API void abg_server_opts_default(abg_server_opts* o);
+ABG_API int abg_server_create(const abg_server_opts* opts, abg_server** out);
+/* Cancels requests not yet started (their poll returns ABG_ECANCELLED), waits for the batches
+ * in flight, frees everything. */
+ABG_API void abg_server_destroy(abg_server* sv);
+/* Queue one request. The graph is validated on the host now; its HOST arrays are read when the
+ * request's batch is uploaded, so they must stay valid until abg_poll returns a final status
+ * for it. Thread-safe. ABG_ENOTADMITTED if its estimated footprint exceeds the budget (the id
+ * is still valid for abg_poll). Requests sharing d_u, x_kind, d, alpha, gamma, t_f, t_g,
+ * oversample and power_iters may be batched together; k and seed are per request, and a
+ * request's result does not depend on what it was batched with. */
+ABG_API int abg_submit(abg_server* sv, const abg_graph_desc* graph, const abg_params* params,
+                       uint64_t* req_id);
+/* Wait up to timeout_us (0: do not wait; < 0: forever) for a request. ABG_OK: labels[n_u]
+ * (host) and *res are filled and the id is released; ABG_PENDING (timeout 0) or
+ * ABG_ETIMEDOUT: not finished; a negative status: the request failed (the id is released). */
+ABG_API int abg_poll(abg_server* sv, uint64_t req_id, int64_t timeout_us, int32_t* labels,
+                     abg_result* res);
+ABG_API int abg_server_get_stats(abg_server* sv, abg_server_stats* out);
+
 /* ---- individual steps (device buffers owned by the caller) --------------- */
 
 /* Eq. 15 / Section 3.2.1: x_out[n_u][ldo] = Gamma Sigma, the top-d SVD of the

@@ -51,6 +51,16 @@ class abg_result(C.Structure):
                 for f, _ in self._fields_}
 
 
+class abg_server_opts(C.Structure):
+    _fields_ = [("device", _i32), ("workers", _i32), ("hbm_budget_bytes", _i64),
+                ("max_batch_graphs", _i32), ("batch_window_us", _i32), ("max_batch_rows", _i64)]
+
+
+class abg_server_stats(C.Structure):
+    _fields_ = [(f, _i64) for f in ("submitted", "completed", "failed", "rejected", "batches",
+                                    "max_batch", "pending", "inflight_bytes", "latency_us_last")]
+
+
 class AbgError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: {detail} (status {status})")
@@ -68,6 +78,15 @@ SIGNATURES = {
     "abg_graph_footprint": (_i64, [_p]),
     "abg_solve_footprint": (_i64, [_p, _p]),
     "abg_cluster": (C.c_int, [_p, _p, _p, _p, _p]),
+    "abg_batch_create": (C.c_int, [_p, _i32, _i32, _p, _p]),
+    "abg_graph_segments": (_i32, [_p]),
+    "abg_batch_cluster": (C.c_int, [_p, _p, _p, _p, _p]),
+    "abg_server_opts_default": (None, [_p]),
+    "abg_server_create": (C.c_int, [_p, _p]),
+    "abg_server_destroy": (None, [_p]),
+    "abg_submit": (C.c_int, [_p, _p, _p, _p]),
+    "abg_poll": (C.c_int, [_p, _u64, _i64, _p, _p]),
+    "abg_server_get_stats": (C.c_int, [_p, _p]),
     "abg_reduce_attributes": (C.c_int, [_p, _i32, _i32, _i32, _u64, _p, _i64, _p]),
     "abg_propagate": (C.c_int, [_p, _p, _i64, _i32, _f64, _i32, _p, _i64, _p]),
     "abg_orthogonal_matrix": (C.c_int, [_u64, _i32, _p, _p]),
@@ -218,6 +237,55 @@ def abg_launch_count() -> int:
     return int(lib().abg_launch_count())
 
 
+def _desc_of(g, keep: list) -> abg_graph_desc:
+    def h(a, dt):
+        arr = _host(a, dt)
+        keep.append(arr)
+        return _ptr(arr)
+
+    d = abg_graph_desc()
+    d.n_u, d.n_v, d.nnz = int(g.n_u), int(g.n_v), int(g.u_ptr[-1])
+    d.u_ptr, d.v_idx = h(g.u_ptr, np.int64), h(g.v_idx, np.int32)
+    d.w = h(g.w, np.float32) if g.w is not None else None
+    d.d_u = int(g.d_u)
+    kind = {"dense_f32": ABG_X_DENSE_F32, "dense_bf16": ABG_X_DENSE_BF16,
+            "csr_f32": ABG_X_CSR_F32}[g.x_kind]
+    d.x_kind = kind
+    if kind == ABG_X_DENSE_F32:
+        d.x = h(g.x, np.float32)
+    elif kind == ABG_X_DENSE_BF16:
+        d.x = h(g.x, np.uint16)
+    else:
+        d.x_ptr, d.x_idx, d.x_val = h(g.x_ptr, np.int64), h(g.x_idx, np.int32), h(g.x_val, np.float32)
+    return d
+
+
+def abg_batch_create(graphs, device: int = 0, stream=None) -> Graph:
+    """Stack several graphs (same d_u and attribute kind) into one batch (segments)."""
+    keep = []
+    arr = (abg_graph_desc * len(graphs))()
+    for i, g in enumerate(graphs):
+        arr[i] = _desc_of(g, keep)
+        arr[i].device = device
+    out = C.c_void_p()
+    _check(lib().abg_batch_create(arr, len(graphs), device, _stream(stream), C.byref(out)),
+           "abg_batch_create")
+    return Graph(out.value, sum(int(g.n_u) for g in graphs), sum(int(g.n_v) for g in graphs),
+                 int(graphs[0].d_u))
+
+
+def abg_batch_cluster(batch: Graph, params_list, labels=None, stream=None):
+    """Solve every graph of a batch; returns (stacked labels, list of abg_result)."""
+    n = len(params_list)
+    ps = (abg_params * n)(*params_list)
+    res = (abg_result * n)()
+    if labels is None:
+        labels = np.empty(batch.n_u, dtype=np.int32)
+    _check(lib().abg_batch_cluster(batch.handle, ps, _stream(stream), _ptr(labels), res),
+           "abg_batch_cluster")
+    return labels, list(res)
+
+
 def abg_solve_footprint(graph: Graph, p: abg_params) -> int:
     return int(lib().abg_solve_footprint(graph.handle, C.byref(p)))
 
@@ -282,3 +350,62 @@ def abg_objective_noalloc(r, n: int, m: int, labels, k: int, stream=None) -> tup
     _check(lib().abg_objective_noalloc(_ptr(r), n, m, _ld(r), _ptr(labels), k, out,
                                        _stream(stream)), "abg_objective_noalloc")
     return float(out[0]), float(out[1])
+
+
+class Server:
+    """Continuous-batching request loop (abg_server_*). Submitted graphs' host arrays are kept
+    alive here until the request is polled to a final status."""
+
+    def __init__(self, device: int = 0, workers: int = 3, hbm_budget_bytes: int = 64 << 30,
+                 max_batch_graphs: int = 64, batch_window_us: int = 0,
+                 max_batch_rows: int = 4 << 20):
+        o = abg_server_opts()
+        lib().abg_server_opts_default(C.byref(o))
+        o.device, o.workers, o.hbm_budget_bytes = device, workers, hbm_budget_bytes
+        o.max_batch_graphs, o.batch_window_us, o.max_batch_rows = (max_batch_graphs,
+                                                                   batch_window_us, max_batch_rows)
+        h = C.c_void_p()
+        _check(lib().abg_server_create(C.byref(o), C.byref(h)), "abg_server_create")
+        self.handle = h.value
+        self._keep = {}
+        self._n_u = {}
+
+    def submit(self, g, p: abg_params) -> int:
+        keep = []
+        d = _desc_of(g, keep)
+        rid = C.c_uint64(0)
+        st = lib().abg_submit(self.handle, C.byref(d), C.byref(p), C.byref(rid))
+        if st == ABG_ENOTADMITTED:
+            return -int(rid.value)
+        _check(st, "abg_submit")
+        self._keep[rid.value] = (keep, d)
+        self._n_u[rid.value] = int(g.n_u)
+        return int(rid.value)
+
+    def poll(self, rid: int, timeout_us: int = -1):
+        """(status, labels or None, abg_result or None)."""
+        n = self._n_u.get(abs(rid), 0)
+        labels = np.empty(max(n, 1), dtype=np.int32)
+        res = abg_result()
+        st = lib().abg_poll(self.handle, abs(rid), timeout_us, _ptr(labels), C.byref(res))
+        if st in (ABG_PENDING, ABG_ETIMEDOUT):
+            return st, None, None
+        self._keep.pop(abs(rid), None)
+        self._n_u.pop(abs(rid), None)
+        return st, (labels[:n] if st == ABG_OK else None), (res if st == ABG_OK else None)
+
+    def stats(self) -> dict:
+        s = abg_server_stats()
+        _check(lib().abg_server_get_stats(self.handle, C.byref(s)), "abg_server_get_stats")
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().abg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -253,6 +253,55 @@ static int upload(abg_graph* g, T** dst, const T* src, int64_t count, cudaStream
   return ABG_OK;
 }
 
+// Transposed CSR of X per segment (row s*d_u + j lists the rows of segment s with column j,
+// in increasing row order) and the stacked column ids s*d_u + j of the row-major CSR.
+static void build_segment_transpose(const abg_graph* g, int64_t d_u, const int64_t* x_ptr,
+                                    const int32_t* x_idx, const float* x_val,
+                                    std::vector<int64_t>& tp, std::vector<int32_t>& ti,
+                                    std::vector<float>& tv, std::vector<int32_t>& xr) {
+  const int64_t rows_t = (int64_t)g->nseg * d_u;
+  const int64_t nnz = x_ptr[g->n_u];
+  tp.assign(rows_t + 1, 0);
+  ti.resize(nnz);
+  tv.resize(nnz);
+  xr.resize(nnz);
+  for (int sg = 0; sg < g->nseg; ++sg)
+    for (int64_t r = g->seg_row0[sg]; r < g->seg_row0[sg] + g->seg_n[sg]; ++r)
+      for (int64_t j = x_ptr[r]; j < x_ptr[r + 1]; ++j) {
+        const int64_t c = (int64_t)sg * d_u + x_idx[j];
+        xr[j] = (int32_t)c;
+        tp[c + 1]++;
+      }
+  for (int64_t c = 0; c < rows_t; ++c) tp[c + 1] += tp[c];
+  std::vector<int64_t> cur(tp.begin(), tp.end() - 1);
+  for (int64_t r = 0; r < g->n_u; ++r)
+    for (int64_t j = x_ptr[r]; j < x_ptr[r + 1]; ++j) {
+      const int64_t p = cur[xr[j]]++;
+      ti[p] = (int32_t)r;
+      tv[p] = x_val[j];
+    }
+}
+
+namespace abg {
+int validate_desc(const abg_graph_desc* d) {
+  ABG_CHECK(d, "null descriptor");
+  ABG_CHECK(d->n_u >= 1 && d->n_v >= 1 && d->n_u < (1ll << 31) && d->n_v < (1ll << 31),
+            "need 1 <= |U|, |V| < 2^31");
+  ABG_CHECK(d->nnz >= 0, "nnz < 0");
+  ABG_CHECK(d->d_u >= 1 && d->d_u <= 65536, "need 1 <= d_u <= 65536");
+  ABG_CHECK(d->x_kind >= ABG_X_DENSE_F32 && d->x_kind <= ABG_X_CSR_F32, "bad x_kind");
+  ABG_TRY(validate_csr(d->u_ptr, d->v_idx, d->w, d->n_u, d->n_v, d->nnz, "CSR"));
+  if (d->x_kind == ABG_X_CSR_F32) {
+    ABG_TRY(validate_csr(d->x_ptr, d->x_idx, nullptr, d->n_u, d->d_u,
+                         d->x_ptr ? d->x_ptr[d->n_u] : 0, "X CSR"));
+    ABG_CHECK(d->x_val, "X CSR: null values");
+  } else {
+    ABG_CHECK(d->x, "dense attributes: null x");
+  }
+  return ABG_OK;
+}
+}  // namespace abg
+
 static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
   ABG_CHECK(d, "null descriptor");
   ABG_CHECK(d->n_u >= 1 && d->n_v >= 1 && d->n_u < (1ll << 31) && d->n_v < (1ll << 31),
@@ -261,6 +310,11 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
   ABG_CHECK(d->d_u >= 1 && d->d_u <= 65536, "need 1 <= d_u <= 65536");
   ABG_CHECK(d->x_kind >= ABG_X_DENSE_F32 && d->x_kind <= ABG_X_CSR_F32, "bad x_kind");
   g->device = d->device;
+  if (g->seg_row0.empty()) {
+    g->nseg = 1;
+    g->seg_row0 = {0};
+    g->seg_n = {d->n_u};
+  }
   g->n_u = d->n_u;
   g->n_v = d->n_v;
   g->nnz = d->nnz;
@@ -360,10 +414,15 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
     std::vector<int64_t> tp;
     std::vector<int32_t> ti;
     std::vector<float> tv;
-    build_csc(d->n_u, d->d_u, g->x_nnz, d->x_ptr, d->x_idx, d->x_val, tp, ti, tv);
-    ABG_TRY(upload(g, &g->xt_ptr, tp.data(), d->d_u + 1, s));
+    std::vector<int32_t> xr;
+    build_segment_transpose(g, d->d_u, d->x_ptr, d->x_idx, d->x_val, tp, ti, tv, xr);
+    ABG_TRY(upload(g, &g->xt_ptr, tp.data(), (int64_t)g->nseg * d->d_u + 1, s));
     ABG_TRY(upload(g, &g->xt_col, ti.data(), g->x_nnz, s));
     ABG_TRY(upload(g, &g->xt_val, tv.data(), g->x_nnz, s));
+    if (g->nseg == 1)
+      g->xr_col = g->x_col;
+    else
+      ABG_TRY(upload(g, &g->xr_col, xr.data(), g->x_nnz, s));
     ABG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   }
   ABG_TRY(build_schedule(g, d->u_ptr, d->n_u, g->sched_u, s));
@@ -410,6 +469,104 @@ ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out
   *out = g;
   return ABG_OK;
 }
+
+// Stack n graphs into one block-diagonal graph whose segments are the inputs.
+ABG_API int abg_batch_create(const abg_graph_desc* descs, int32_t n, int32_t device, void* stream,
+                             abg_graph** out) {
+  if (!out) {
+    set_error("null output pointer");
+    return ABG_EINVAL;
+  }
+  *out = nullptr;
+  ABG_CHECK(descs && n >= 1, "need at least one graph");
+  const int32_t d_u = descs[0].d_u, kind = descs[0].x_kind;
+  int64_t nu = 0, nv = 0, nnz = 0, xnnz = 0;
+  bool weighted = false;
+  for (int i = 0; i < n; ++i) {
+    const abg_graph_desc& e = descs[i];
+    ABG_CHECK(e.d_u == d_u && e.x_kind == kind,
+              "batched graphs need the same attribute width and storage kind");
+    ABG_CHECK(e.n_u >= 1 && e.n_v >= 1 && e.nnz >= 0 && e.u_ptr && e.v_idx, "graph %d: bad sizes", i);
+    ABG_CHECK(e.u_ptr[0] == 0 && e.u_ptr[e.n_u] == e.nnz, "graph %d: bad CSR pointers", i);
+    if (kind == ABG_X_CSR_F32) {
+      ABG_CHECK(e.x_ptr && e.x_idx && e.x_val && e.x_ptr[0] == 0, "graph %d: bad X CSR", i);
+      xnnz += e.x_ptr[e.n_u];
+    } else {
+      ABG_CHECK(e.x, "graph %d: null attributes", i);
+    }
+    weighted |= e.w != nullptr;
+    nu += e.n_u;
+    nv += e.n_v;
+    nnz += e.nnz;
+  }
+  ABG_CHECK(nu < (1ll << 31) && nv < (1ll << 31), "batch too large: |U|, |V| must stay < 2^31");
+  const size_t esz = kind == ABG_X_DENSE_F32 ? 4 : 2;
+  std::vector<int64_t> u_ptr(nu + 1), x_ptr;
+  std::vector<int32_t> v_idx(nnz), x_idx;
+  std::vector<float> w, x_val;
+  std::vector<unsigned char> x_dense;
+  if (weighted) w.resize(nnz);
+  if (kind == ABG_X_CSR_F32) {
+    x_ptr.resize(nu + 1);
+    x_idx.resize(xnnz);
+    x_val.resize(xnnz);
+  } else {
+    x_dense.resize(esz * nu * d_u);
+  }
+  abg_graph* g = new abg_graph();
+  int64_t ro = 0, vo = 0, eo = 0, xo = 0;
+  u_ptr[0] = 0;
+  if (kind == ABG_X_CSR_F32) x_ptr[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const abg_graph_desc& e = descs[i];
+    g->seg_row0.push_back(ro);
+    g->seg_n.push_back(e.n_u);
+    for (int64_t r = 0; r < e.n_u; ++r) u_ptr[ro + r + 1] = eo + e.u_ptr[r + 1];
+    for (int64_t j = 0; j < e.nnz; ++j) {
+      v_idx[eo + j] = (int32_t)(vo + e.v_idx[j]);
+      if (weighted) w[eo + j] = e.w ? e.w[j] : 1.f;
+    }
+    if (kind == ABG_X_CSR_F32) {
+      for (int64_t r = 0; r < e.n_u; ++r) x_ptr[ro + r + 1] = xo + e.x_ptr[r + 1];
+      const int64_t en = e.x_ptr[e.n_u];
+      std::copy(e.x_idx, e.x_idx + en, x_idx.begin() + xo);
+      std::copy(e.x_val, e.x_val + en, x_val.begin() + xo);
+      xo += en;
+    } else {
+      memcpy(x_dense.data() + esz * ro * d_u, e.x, esz * e.n_u * d_u);
+    }
+    ro += e.n_u;
+    vo += e.n_v;
+    eo += e.nnz;
+  }
+  g->nseg = n;
+  abg_graph_desc u{};
+  u.n_u = nu;
+  u.n_v = nv;
+  u.nnz = nnz;
+  u.u_ptr = u_ptr.data();
+  u.v_idx = v_idx.data();
+  u.w = weighted ? w.data() : nullptr;
+  u.d_u = d_u;
+  u.x_kind = kind;
+  if (kind == ABG_X_CSR_F32) {
+    u.x_ptr = x_ptr.data();
+    u.x_idx = x_idx.data();
+    u.x_val = x_val.data();
+  } else {
+    u.x = x_dense.data();
+  }
+  u.device = device;
+  int st = create_impl(&u, (cudaStream_t)stream, g);
+  if (st != ABG_OK) {
+    abg_destroy(g);
+    return st;
+  }
+  *out = g;
+  return ABG_OK;
+}
+
+ABG_API int32_t abg_graph_segments(const abg_graph* g) { return g ? g->nseg : 0; }
 
 ABG_API void abg_destroy(abg_graph* g) {
   if (!g) return;

@@ -1,6 +1,9 @@
 // Internal interfaces between the library's translation units.
 #pragma once
 
+#include <vector>
+
+#include "batch.cuh"
 #include "common.cuh"
 
 // Device-resident graph (Section 2.1): both CSR (rows = U) and CSC (rows = V)
@@ -27,9 +30,14 @@ struct abg_graph {
   int64_t* x_ptr = nullptr;
   int32_t* x_col = nullptr;
   float* x_val = nullptr;
-  int64_t* xt_ptr = nullptr;
-  int32_t* xt_col = nullptr;
+  int64_t* xt_ptr = nullptr;   // transposed CSR of X per segment: row s*d_u + j lists the
+  int32_t* xt_col = nullptr;   //   rows of segment s holding column j (global row ids)
   float* xt_val = nullptr;
+  int32_t* xr_col = nullptr;   // X CSR columns as s*d_u + j (the stacked test-block rows)
+  // segments: a graph made by abg_batch_create stacks independent graphs
+  // (block-diagonal union); segment s owns U rows [seg_row0[s], +seg_n[s])
+  int nseg = 1;
+  std::vector<int64_t> seg_row0, seg_n;
   // SpMM schedules: light rows in decreasing-degree order, heavy rows split
   // into fixed-size edge chunks whose partial sums are reduced in order.
   struct Schedule {
@@ -56,6 +64,8 @@ constexpr int kHeavyRow = 1024;    // rows with more edges are split
 
 // ---- graph.cu ---------------------------------------------------------------
 int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s);
+// host-only validation of a graph descriptor (CSR, optional CSC, weights, attributes)
+int validate_desc(const abg_graph_desc* d);
 
 // ---- spmm.cu ----------------------------------------------------------------
 // Algorithm 1 propagation + Eq. 2 on device buffers. Exactly one of x_f32 /
@@ -71,78 +81,124 @@ int csr_to_dense(const int64_t* ptr, const int32_t* col, const float* val, int64
 int bf16_to_f32(const __nv_bfloat16* x, int64_t ldx, int64_t rows, int cols, float* out,
                 int64_t ldo, cudaStream_t s);
 
-// ---- dense.cu ---------------------------------------------------------------
+// ---- dense.cu (row spaces of batch.cuh; a plain solve is one segment) -------
 enum class Epi : int {
   Store = 0,        // C = acc
   Relu = 1,         // C = max(acc, 0)
-  SignRelu = 2,     // C = max(sign[col] * acc, 0)
-  Sign = 3,         // C = sign[col] * acc
-  PhiUpdate = 4,    // C = phi * sqrt(max(aux,0)/acc) (acc > 0) else 0   [Eq. 17]
+  SignRelu = 2,     // C = max(sign_s[col] * acc, 0)
+  Sign = 3,         // C = sign_s[col] * acc
+  PhiUpdate = 4,    // C = phi * sqrt(max(P,0)/acc) (acc > 0) else 0   [Eq. 17]
 };
-// C[M][ldc] = A[M][lda] (M x K) * B[K][ldb] (K x N) with the epilogue.
-// aux/aux2: PhiUpdate reads P=aux[M][ldaux] and phi=aux2[M][ldaux2]; sign[N] for Sign*.
-int gemm_nn(int64_t M, int N, int K, const float* A, int64_t lda, const float* B, int64_t ldb,
-            float* C, int64_t ldc, Epi epi, const float* aux, int64_t ldaux, const float* aux2,
-            int64_t ldaux2, const float* sign, cudaStream_t s);
-// C[K][N] (FP64, row stride ldc) = A[M][lda]^T (K x M) * B[M][ldb] (M x N), reduction over
-// the long dimension M in fixed-size row chunks (FP32 products, FP64 accumulation).
-int gemm_tn(int64_t M, int K, int N, const float* A, int64_t lda, const float* B, int64_t ldb,
-            double* C, int64_t ldc, Scratch& scr, cudaStream_t s);
-// colsum[N] (FP64) of A[M][lda]
-int column_sums(int64_t M, int N, const float* A, int64_t lda, double* out, Scratch& scr,
+// C = A B_s for the rows of segment s (B_s at B + s*b_seg; per-segment N_s/K_s when segN/segK
+// are given, else N/K). aux = P, aux2 = phi for PhiUpdate; sign_s at sign + s*sign_seg.
+struct NN {
+  const float* A = nullptr;
+  int64_t lda = 0;
+  const float* B = nullptr;
+  int64_t ldb = 0, b_seg = 0;
+  float* C = nullptr;
+  int64_t ldc = 0;
+  int N = 0, K = 0;
+  const int* segN = nullptr;
+  const int* segK = nullptr;
+  Epi epi = Epi::Store;
+  const float* aux = nullptr;
+  int64_t ldaux = 0;
+  const float* aux2 = nullptr;
+  int64_t ldaux2 = 0;
+  const float* sign = nullptr;
+  int64_t sign_seg = 0;
+  // random features: R'[i] = out_scale (sin || cos)(in_scale acc), per-tile column sums
+  bool sincos = false;
+  float in_scale = 1.f, out_scale = 1.f;
+  double* colsum_part = nullptr;
+  // NCI scores: row argmax into labels (+ margin), per-segment change / min-margin counters
+  bool argmax = false;
+  int32_t* labels = nullptr;
+  float* margin = nullptr;
+  int first = 0;
+  int* changes = nullptr;
+  unsigned* minbits = nullptr;
+};
+int gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s);
+// C_s (K_s x N_s, FP64, at C + s*c_seg, row stride ldc) = A^T B over the rows of segment s.
+struct TN {
+  const float* A = nullptr;
+  int64_t lda = 0;
+  const float* B = nullptr;
+  int64_t ldb = 0;
+  int K = 0, N = 0;
+  const int* segK = nullptr;
+  const int* segN = nullptr;
+  double* C = nullptr;
+  int64_t ldc = 0, c_seg = 0;
+};
+int gemm_tn(const RowSpace& rs, const TN& a, cudaStream_t s);
+// colsum_s[N] (FP64, at out + s*oseg) of A over the rows of segment s
+int column_sums(const RowSpace& rs, int N, const float* A, int64_t lda, double* out, int64_t oseg,
                 cudaStream_t s);
-// Eqs. 13-14 on zhat (n x d) with Qt[d][d] = Q^T (float), result in R[n][ldr] (2d wide).
-int random_features(const float* zhat, int64_t n, int d, int64_t ldz, const float* qt,
-                    float* R, int64_t ldr, int* clamped_dev, Scratch& scr, cudaStream_t s);
-// Eq. 16 on small matrices: H[m][ldh] <- H * max(A,0) / (H G) (A, G FP64).
-int nmf_update_h(int m, int k, float* H, int64_t ldh, const double* A, int64_t lda,
-                 const double* G, int64_t ldg, cudaStream_t s);
-// Algorithm 3 (all t_g passes) on phi (n x k).
-int nci_run(const float* phi, int64_t n, int k, int64_t ldphi, int t_g, int32_t* labels,
-            float* margin, double* t_out, int* last_changes_host, float* min_margin_host,
-            int* empty_host, Scratch& scr, cudaStream_t s);
-// Eq. 8 (objective, trace) through per-cluster sums.
-int objective(const float* R, int64_t n, int m, int64_t ldr, const int32_t* labels, int k,
-              double* obj_host, Scratch& scr, cudaStream_t s);
+// Eqs. 13-14: R (2d wide) from zhat (d wide) with Qt_s = Q_s^T at qt + s*d*ldq; per-segment r;
+// clamped_dev[s] counts clamped rows.
+int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, const float* qt,
+                    int64_t ldq, float* R, int64_t ldr, int* clamped_dev, cudaStream_t s);
+// Eq. 16 per segment (H_s at H + s*hseg, m x k_s; A_s, G_s FP64 slabs).
+int nmf_update_h(int nseg, int m, const int* segk, int kmax, float* H, int64_t ldh, int64_t hseg,
+                 const double* A, int64_t lda, int64_t aseg, const double* G, int64_t ldg,
+                 int64_t gseg, cudaStream_t s);
+// Algorithm 3 (all t_g passes) per segment. counters (device, 3*nseg ints): last-pass label
+// changes, minimum margin (float bits), empty clusters.
+int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ldphi, int t_g,
+            int32_t* labels, float* margin, double* t_out, int* counters, cudaStream_t s);
+// Eq. 8 per segment: out_dev[2s] = objective, out_dev[2s+1] = Tr(Y^T R R^T Y).
+int objective(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int64_t ldr,
+              const int32_t* labels, double* out_dev, cudaStream_t s);
 
 // ---- linalg.cu --------------------------------------------------------------
-// Gaussian matrix (rows x cols, row stride ld) from (seed, stream id) as described in abg.h.
-int gaussian_f64(uint64_t seed, int stream_id, int rows, int cols, double* out, int64_t ld,
-                 cudaStream_t s);
-int gaussian_f32(uint64_t seed, int stream_id, int rows, int cols, float* out, int64_t ld,
-                 cudaStream_t s);
-// Q (d x d, FP64) = orthogonal factor of QR(G) with positive diag(R); G from ABG_STREAM_G.
-int orthogonal_matrix(uint64_t seed, int d, double* q, cudaStream_t s);
-// CholeskyQR2 in place: Y[M][ldy] (M x l) -> orthonormal columns. breakdowns (device int) counts
-// non-positive pivots.
-int cholqr2(int64_t M, int l, float* Y, int64_t ldy, float* tmp, int64_t ldt, int* breakdowns,
-            Scratch& scr, cudaStream_t s);
-// Truncated randomized SVD of A (n x m, dense float) or of a CSR matrix (with its transpose).
-struct RsvdOut {
-  float* left = nullptr;        // n x k, row stride ldl: max(Gamma,0) / Gamma*Sigma / ...
-  int64_t ldl = 0;
-  int left_mode = 0;            // 0: max(Gamma,0)   1: Gamma*Sigma (signed)
-  float* right = nullptr;       // m x k, row stride ldr: max(Psi*Sigma, 0) (may be null)
-  int64_t ldr = 0;
-  double* sigma = nullptr;      // k (device, may be null)
-};
+// Gaussian matrix (rows x cols, row stride ld) of each segment from (seeds[s], stream id); the
+// segment's block sits at out + s*oseg; columns >= cols_s (segcols) are set to 0.
+int gaussian_f64(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols, double* out,
+                 int64_t ld, int64_t oseg, cudaStream_t s);
+int gaussian_f32(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols,
+                 const int* segcols, float* out, int64_t ld, int64_t oseg, cudaStream_t s);
+// Q_s (d x d, FP64, at q + s*d*d) = orthogonal factor of QR(G_s), diag(R) > 0, G_s drawn from
+// seeds[s] on ABG_STREAM_G.
+int orthogonal_matrices(int nseg, const uint64_t* seeds, int d, double* q, cudaStream_t s);
+// CholeskyQR2 in place on Y (rows of each segment, l_s columns, row stride ldy).
+int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy, float* tmp,
+            int64_t ldt, int* breakdowns, cudaStream_t s);
+// Truncated randomized SVD per segment (randomized subspace iteration).
 struct RsvdIn {
-  int64_t n = 0;
-  int m = 0;
-  const float* A = nullptr;     // dense n x m
+  const RowSpace* rows = nullptr;  // rows of A (one segment per problem)
+  int m = 0;                       // columns of A (same for every segment)
+  const float* A = nullptr;        // dense rows x m
   int64_t lda = 0;
-  const int64_t* ptr = nullptr; // or CSR (n x m) + CSR of the transpose (m x n)
+  // or a CSR whose column j of segment s is stored as s*m + j, and the CSR of the
+  // transposes with row s*m + j listing segment s's rows (global row ids)
+  const int64_t* ptr = nullptr;
   const int32_t* col = nullptr;
   const float* val = nullptr;
   const int64_t* tptr = nullptr;
   const int32_t* tcol = nullptr;
   const float* tval = nullptr;
 };
-int rsvd(const RsvdIn& in, int k, int oversample, int power_iters, uint64_t seed, int stream_id,
-         const RsvdOut& out, int* breakdowns, Scratch& scr, cudaStream_t s);
+struct RsvdOut {
+  float* left = nullptr;        // rows x (k_s or kfixed), row stride ldl
+  int64_t ldl = 0;
+  int left_mode = 0;            // 0: max(Gamma, 0)   1: Gamma * Sigma
+  float* right = nullptr;       // per segment m x k_s (max(Psi Sigma, 0)), at right + s*rseg
+  int64_t ldr = 0, rseg = 0;
+  double* sigma = nullptr;      // per segment k_s values at sigma + s*sseg (may be null)
+  int64_t sseg = 0;
+};
+// k per segment: ss.k (left_mode 0) or the uniform kfixed (left_mode 1, ss.k ignored);
+// l per segment: ss.l; seeds: ss.seed.
+int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int stream_id,
+         const RsvdOut& out, int* breakdowns, cudaStream_t s);
 int transpose_f64_to_f32(const double* a, int rows, int cols, int64_t lda, float* out,
                          int64_t ldo, cudaStream_t s);
-int convert_f64_to_f32(const double* a, int rows, int cols, int64_t lda, float* out, int64_t ldo,
-                       cudaStream_t s);
+int convert_f64_to_f32(const double* a, int64_t rows, int cols, int64_t lda, float* out,
+                       int64_t ldo, cudaStream_t s);
+// per-segment transpose of d x d FP64 blocks into FP32 (Qt_s = Q_s^T, row stride ldo)
+int transpose_blocks(int nseg, int d, const double* q, float* qt, int64_t ldo, cudaStream_t s);
 
 }  // namespace abg

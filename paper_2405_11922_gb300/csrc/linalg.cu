@@ -1,12 +1,14 @@
-// Random matrices and small dense linear algebra of the method:
+// Random matrices and small dense linear algebra of the method, per segment of
+// a batch (a plain solve is one segment):
 //   * Gaussian draws from Philox4x32-10 (Salmon et al., SC'11) + Box-Muller
-//     on the device (G of Algorithm 1, the randomized-SVD test matrices);
+//     on the device (G of Algorithm 1, the randomized-SVD test matrices),
+//     keyed by each segment's own seed;
 //   * Q = orthogonal factor of QR(G) (Algorithm 1), by CholeskyQR2 in FP64;
 //   * CholeskyQR2 of tall FP32 blocks (FP64 Gram / Cholesky, FP32 apply);
 //   * the truncated randomized SVD of Halko, Martinsson and Tropp (subspace
 //     iteration) used by Algorithm 2's seeding (Eq. 18) and by the attribute
 //     reduction of Section 3.2.1 (Eq. 15): the small l x l eigenproblem runs
-//     as a one-CTA parallel cyclic Jacobi in FP64.
+//     as a one-CTA parallel cyclic Jacobi in FP64 per segment.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -34,10 +36,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// Segment blockIdx.y's matrix is rows x cols_s (cols_s = segcols[s], else cols): its entry
+// e = r * cols_s + c comes from the counter mapping of abg.h, so a segment draws the same
+// numbers whatever the batch's widest segment; columns cols_s..cols-1 are set to 0.
 template <class T>
-__global__ void k_gaussian(uint64_t seed, uint32_t stream_id, int rows, int cols, T* out,
-                           int64_t ld) {
-  const int64_t total = (int64_t)rows * cols;
+__global__ void k_gaussian(const uint64_t* __restrict__ seeds, uint32_t stream_id, int rows,
+                           int cols, const int* __restrict__ segcols, T* out, int64_t ld,
+                           int64_t oseg) {
+  const int sg = blockIdx.y;
+  const uint64_t seed = seeds[sg];
+  const int cs = segcols ? segcols[sg] : cols;
+  T* o = out + sg * oseg;
+  const int64_t total = (int64_t)rows * cs;
   const int64_t nb = (total + 3) / 4;
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -50,51 +60,73 @@ __global__ void k_gaussian(uint64_t seed, uint32_t stream_id, int rows, int cols
 #pragma unroll
     for (int a = 0; a < 4; a += 2) {
       const double rad = sqrt(-2.0 * log(u[a]));
-      double sn, cs;
-      sincospi(2.0 * u[a + 1], &sn, &cs);
-      z[a] = rad * cs;
+      double sn, cn;
+      sincospi(2.0 * u[a + 1], &sn, &cn);
+      z[a] = rad * cn;
       z[a + 1] = rad * sn;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t e = 4 * b + j;
-      if (e < total) out[(e / cols) * ld + (e % cols)] = (T)z[j];
+      if (e < total) o[(e / cs) * ld + (e % cs)] = (T)z[j];
     }
+  }
+  if (cs < cols) {
+    const int64_t pad = (int64_t)rows * (cols - cs);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < pad;
+         q += (int64_t)gridDim.x * blockDim.x)
+      o[(q / (cols - cs)) * ld + cs + (q % (cols - cs))] = (T)0;
   }
 }
 
-int gaussian_f64(uint64_t seed, int stream_id, int rows, int cols, double* out, int64_t ld,
-                 cudaStream_t s) {
+int gaussian_f64(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols, double* out,
+                 int64_t ld, int64_t oseg, cudaStream_t s) {
   const int64_t nb = ((int64_t)rows * cols + 3) / 4;
-  k_gaussian<double><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, 256), 4096)),
-                       256, 0, s>>>(seed, (uint32_t)stream_id, rows, cols, out, ld); ::abg::note_launch();
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, 256), 2048)),
+            (unsigned)nseg);
+  k_gaussian<double><<<grid, 256, 0, s>>>(seeds, (uint32_t)stream_id, rows, cols, nullptr, out,
+                                          ld, oseg);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
-int gaussian_f32(uint64_t seed, int stream_id, int rows, int cols, float* out, int64_t ld,
-                 cudaStream_t s) {
+int gaussian_f32(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols,
+                 const int* segcols, float* out, int64_t ld, int64_t oseg, cudaStream_t s) {
   const int64_t nb = ((int64_t)rows * cols + 3) / 4;
-  k_gaussian<float><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, 256), 4096)),
-                      256, 0, s>>>(seed, (uint32_t)stream_id, rows, cols, out, ld); ::abg::note_launch();
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nb, 256), 2048)),
+            (unsigned)nseg);
+  k_gaussian<float><<<grid, 256, 0, s>>>(seeds, (uint32_t)stream_id, rows, cols, segcols, out,
+                                         ld, oseg);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// One-CTA Cholesky G = R^T R (R upper, positive diagonal) and R^-1, FP64.
-// A non-positive (or relatively negligible) pivot zeroes that row of R and
-// that column of R^-1 (the column of Q it would produce is dropped) and is
-// counted in *breakdowns.
-// work: l*l doubles (R), rinv64: l*l doubles; rinv32 (optional): l x ldr floats.
+// One CTA per segment: Cholesky G_s = R^T R (R upper, positive diagonal) and
+// R^-1 in FP64 (shared memory when both triangles fit). A non-positive (or
+// relatively negligible) pivot zeroes that row of R and that column of R^-1
+// (the column of Q it would produce is dropped) and is counted in *breakdowns.
+// Slabs: G_s at G + s*gseg (row stride ldg); R_s, Ri_s at R + s*l*l with l the
+// segment's size (row stride l); ri32_s (optional) at ri32 + s*r32seg.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restrict__ G, int64_t ldg,
-                                                   double* __restrict__ Rg, double* __restrict__ Rig,
-                                                   float* __restrict__ ri32, int64_t ldr32,
-                                                   int* __restrict__ breakdowns, int in_smem) {
+__global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl, int lfix,
+                                                   const double* __restrict__ Gall, int64_t ldg,
+                                                   int64_t gseg, double* __restrict__ Rall,
+                                                   double* __restrict__ Riall, int64_t rseg,
+                                                   float* __restrict__ ri32all, int64_t ldr32,
+                                                   int64_t r32seg, int* __restrict__ breakdowns,
+                                                   int in_smem) {
   extern __shared__ double csm[];
-  double* R = in_smem ? csm : Rg;                    // l x l, upper triangle used
-  double* Ri = in_smem ? csm + (int64_t)l * l : Rig; // l x l
+  const int sg = blockIdx.x;
+  const int l = segl ? segl[sg] : lfix;
+  const double* G = Gall + sg * gseg;
+  double* Rg = Rall + sg * rseg;
+  double* Rig = Riall + sg * rseg;
+  float* ri32 = ri32all ? ri32all + sg * r32seg : nullptr;
+  double* R = in_smem ? csm : Rg;
+  double* Ri = in_smem ? csm + (int64_t)l * l : Rig;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
   __shared__ double s_piv;
@@ -122,20 +154,17 @@ __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restri
     }
     __syncthreads();
     const double piv = s_piv;
-    // row j of R: R[j][j] = piv, R[j][c] = A[j][c] / piv (all zero after a breakdown)
     for (int c = j + tid; c < l; c += nt) {
       const double v = R[(int64_t)j * l + c];
       R[(int64_t)j * l + c] = piv > 0.0 ? (c == j ? piv : v / piv) : 0.0;
     }
     __syncthreads();
-    // trailing update A[r][c] -= R[j][r] R[j][c] for j < r <= c: a warp per row
     for (int r = j + 1 + warp; r < l; r += nw) {
       const double rjr = R[(int64_t)j * l + r];
       for (int c = r + lane; c < l; c += 32) R[(int64_t)r * l + c] -= rjr * R[(int64_t)j * l + c];
     }
     __syncthreads();
   }
-  // inverse of the upper-triangular R, one warp per column (back substitution)
   for (int j = warp; j < l; j += nw) {
     for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
     __syncwarp();
@@ -151,7 +180,6 @@ __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restri
       }
       __syncwarp();
     }
-    // a dropped pivot on the diagonal zeroes this column of R^-1
     if (R[(int64_t)j * l + j] <= 0.0)
       for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
   }
@@ -163,68 +191,71 @@ __global__ void __launch_bounds__(1024) k_chol_inv(int l, const double* __restri
   }
 }
 
-// Launch k_chol_inv with both triangles in shared memory when they fit.
-static int chol_inv(int l, const double* G, int64_t ldg, double* R, double* Ri, float* ri32,
-                    int64_t ldr32, int* breakdowns, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 2 * (size_t)l * l;
+static int chol_inv(int nseg, const int* segl, int lmax, const double* G, int64_t ldg, int64_t gseg,
+                    double* R, double* Ri, int64_t rseg, float* ri32, int64_t ldr32, int64_t r32seg,
+                    int* breakdowns, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 2 * (size_t)lmax * lmax;
   const int in_smem = smem <= 200 * 1024;
   if (in_smem)
     ABG_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  k_chol_inv<<<1, 1024, in_smem ? smem : 0, s>>>(l, G, ldg, R, Ri, ri32, ldr32, breakdowns,
-                                                 in_smem);
-  ::abg::note_launch();
+  k_chol_inv<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(segl, lmax, G, ldg, gseg, R, Ri, rseg,
+                                                              ri32, ldr32, r32seg, breakdowns,
+                                                              in_smem);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Small FP64 products (d x d and l x l matrices)
+// Small FP64 products per segment
 // ---------------------------------------------------------------------------
-// C[i][j] = sum_r A[r][i] B[r][j]   (A: rows x ca, B: rows x cb)
-__global__ void k_small_tn64(int rows, int ca, int cb, const double* __restrict__ A, int64_t lda,
-                             const double* __restrict__ B, int64_t ldb, double* __restrict__ C,
-                             int64_t ldc) {
+// C_s[i][j] = sum_{r < rows} A_s[r][i] B_s[r][j] for i < ca_s, j < cb_s
+__global__ void k_small_tn64(int rows, const int* __restrict__ sca, int ca, const int* __restrict__ scb,
+                             int cb, const double* __restrict__ A, int64_t lda, int64_t aseg,
+                             const double* __restrict__ B, int64_t ldb, int64_t bseg,
+                             double* __restrict__ C, int64_t ldc, int64_t cseg) {
+  const int sg = blockIdx.y;
+  const int cas = sca ? sca[sg] : ca, cbs = scb ? scb[sg] : cb;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)ca * cb) return;
   const int i = (int)(q / cb), j = (int)(q % cb);
-  double s = 0.0;
-  for (int r = 0; r < rows; ++r) s += A[(int64_t)r * lda + i] * B[(int64_t)r * ldb + j];
-  C[(int64_t)i * ldc + j] = s;
+  if (i >= cas || j >= cbs) return;
+  const double* As = A + sg * aseg;
+  const double* Bs = B + sg * bseg;
+  double acc = 0.0;
+  for (int r = 0; r < rows; ++r) acc += As[(int64_t)r * lda + i] * Bs[(int64_t)r * ldb + j];
+  C[sg * cseg + (int64_t)i * ldc + j] = acc;
 }
 
-// C[i][j] = sum_p A[i][p] B[p][j]   (A: ra x inner, B: inner x cb)
-__global__ void k_small_nn64(int ra, int inner, int cb, const double* __restrict__ A, int64_t lda,
-                             const double* __restrict__ B, int64_t ldb, double* __restrict__ C,
-                             int64_t ldc) {
+// C_s[i][j] = sum_{p < inner_s} A_s[i][p] B_s[p][j] for i < ra, j < cb_s
+__global__ void k_small_nn64(int ra, const int* __restrict__ sinner, int inner,
+                             const int* __restrict__ scb, int cb, const double* __restrict__ A,
+                             int64_t lda, int64_t aseg, const double* __restrict__ B, int64_t ldb,
+                             int64_t bseg, double* __restrict__ C, int64_t ldc, int64_t cseg) {
+  const int sg = blockIdx.y;
+  const int ins = sinner ? sinner[sg] : inner, cbs = scb ? scb[sg] : cb;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (int64_t)ra * cb) return;
   const int i = (int)(q / cb), j = (int)(q % cb);
-  double s = 0.0;
-  for (int p = 0; p < inner; ++p) s += A[(int64_t)i * lda + p] * B[(int64_t)p * ldb + j];
-  C[(int64_t)i * ldc + j] = s;
+  if (j >= cbs) return;
+  const double* As = A + sg * aseg;
+  const double* Bs = B + sg * bseg;
+  double acc = 0.0;
+  for (int p = 0; p < ins; ++p) acc += As[(int64_t)i * lda + p] * Bs[(int64_t)p * ldb + j];
+  C[sg * cseg + (int64_t)i * ldc + j] = acc;
 }
 
-static void small_tn64(int rows, int ca, int cb, const double* A, int64_t lda, const double* B,
-                       int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
-  k_small_tn64<<<(unsigned)ceil_div((int64_t)ca * cb, 128), 128, 0, s>>>(rows, ca, cb, A, lda, B,
-                                                                        ldb, C, ldc); ::abg::note_launch();
-}
-static void small_nn64(int ra, int inner, int cb, const double* A, int64_t lda, const double* B,
-                       int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
-  k_small_nn64<<<(unsigned)ceil_div((int64_t)ra * cb, 128), 128, 0, s>>>(ra, inner, cb, A, lda, B,
-                                                                        ldb, C, ldc); ::abg::note_launch();
-}
-
-__global__ void k_f64_to_f32(int rows, int cols, const double* __restrict__ a, int64_t lda,
+__global__ void k_f64_to_f32(int64_t rows, int cols, const double* __restrict__ a, int64_t lda,
                              float* __restrict__ o, int64_t ldo, int transpose) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)rows * cols) return;
-  const int i = (int)(q / cols), j = (int)(q % cols);
+  if (q >= rows * cols) return;
+  const int64_t i = q / cols;
+  const int j = (int)(q % cols);
   if (transpose)
-    o[(int64_t)j * ldo + i] = (float)a[(int64_t)i * lda + j];
+    o[(int64_t)j * ldo + i] = (float)a[i * lda + j];
   else
-    o[(int64_t)i * ldo + j] = (float)a[(int64_t)i * lda + j];
+    o[i * ldo + j] = (float)a[i * lda + j];
 }
 
 __global__ void k_f32_to_f64(int64_t rows, int cols, const float* __restrict__ a, int64_t lda,
@@ -236,44 +267,73 @@ __global__ void k_f32_to_f64(int64_t rows, int cols, const float* __restrict__ a
   o[i * ldo + j] = (double)a[i * lda + j];
 }
 
+// Qt_s = Q_s^T (FP32) for nseg d x d FP64 blocks
+__global__ void k_transpose_blocks(int nseg, int d, const double* __restrict__ q,
+                                   float* __restrict__ qt, int64_t ldo) {
+  const int64_t total = (int64_t)nseg * d * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = e / ((int64_t)d * d);
+    const int rem = (int)(e % ((int64_t)d * d));
+    const int i = rem / d, j = rem % d;
+    qt[sg * d * ldo + (int64_t)j * ldo + i] = (float)q[e];
+  }
+}
+
 int transpose_f64_to_f32(const double* a, int rows, int cols, int64_t lda, float* out, int64_t ldo,
                          cudaStream_t s) {
   k_f64_to_f32<<<(unsigned)ceil_div((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, a, lda,
-                                                                            out, ldo, 1); ::abg::note_launch();
+                                                                            out, ldo, 1);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
-int convert_f64_to_f32(const double* a, int rows, int cols, int64_t lda, float* out, int64_t ldo,
-                       cudaStream_t s) {
-  k_f64_to_f32<<<(unsigned)ceil_div((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, a, lda,
-                                                                            out, ldo, 0); ::abg::note_launch();
+int convert_f64_to_f32(const double* a, int64_t rows, int cols, int64_t lda, float* out,
+                       int64_t ldo, cudaStream_t s) {
+  if (rows * cols == 0) return ABG_OK;
+  k_f64_to_f32<<<(unsigned)ceil_div(rows * cols, 256), 256, 0, s>>>(rows, cols, a, lda, out, ldo,
+                                                                   0);
+  note_launch();
+  ABG_LAUNCH_CHECK();
+  return ABG_OK;
+}
+
+int transpose_blocks(int nseg, int d, const double* q, float* qt, int64_t ldo, cudaStream_t s) {
+  const int64_t total = (int64_t)nseg * d * d;
+  k_transpose_blocks<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 65535), 256, 0, s>>>(
+      nseg, d, q, qt, ldo);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Q of Algorithm 1: CholeskyQR2 of G in FP64 (unique Q with diag(R) > 0)
+// Q_s of Algorithm 1: CholeskyQR2 of G_s in FP64 (unique Q with diag(R) > 0)
 // ---------------------------------------------------------------------------
-int orthogonal_matrix(uint64_t seed, int d, double* q, cudaStream_t s) {
+int orthogonal_matrices(int nseg, const uint64_t* seeds, int d, double* q, cudaStream_t s) {
   ABG_CHECK(d >= 1 && d <= kMaxD, "orthogonal_matrix: need 1 <= d <= %d", kMaxD);
   Scratch scr(s);
+  const int64_t dd = (int64_t)d * d;
   double *G, *Gram, *R, *Ri, *T;
-  ABG_TRY(scr.get(&G, (size_t)d * d));
-  ABG_TRY(scr.get(&Gram, (size_t)d * d));
-  ABG_TRY(scr.get(&R, (size_t)d * d));
-  ABG_TRY(scr.get(&Ri, (size_t)d * d));
-  ABG_TRY(scr.get(&T, (size_t)d * d));
+  ABG_TRY(scr.get(&G, (size_t)nseg * dd));
+  ABG_TRY(scr.get(&Gram, (size_t)nseg * dd));
+  ABG_TRY(scr.get(&R, (size_t)nseg * dd));
+  ABG_TRY(scr.get(&Ri, (size_t)nseg * dd));
+  ABG_TRY(scr.get(&T, (size_t)nseg * dd));
   int* bd;
   ABG_TRY(scr.get(&bd, 1));
   ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
-  ABG_TRY(gaussian_f64(seed, ABG_STREAM_G, d, d, G, d, s));
+  ABG_TRY(gaussian_f64(nseg, seeds, ABG_STREAM_G, d, d, G, d, dd, s));
   double* src = G;
-  double* dst = T;
+  dim3 grid((unsigned)ceil_div(dd, 128), (unsigned)nseg);
   for (int pass = 0; pass < 2; ++pass) {
-    small_tn64(d, d, d, src, d, src, d, Gram, d, s);
-    ABG_TRY(chol_inv(d, Gram, d, R, Ri, nullptr, 0, bd, s));
-    small_nn64(d, d, d, src, d, Ri, d, pass == 1 ? q : dst, d, s);
+    k_small_tn64<<<grid, 128, 0, s>>>(d, nullptr, d, nullptr, d, src, d, dd, src, d, dd, Gram, d, dd);
+    note_launch();
+    ABG_TRY(chol_inv(nseg, nullptr, d, Gram, d, dd, R, Ri, dd, nullptr, 0, 0, bd, s));
+    double* dst = pass == 1 ? q : T;
+    k_small_nn64<<<grid, 128, 0, s>>>(d, nullptr, d, nullptr, d, src, d, dd, Ri, d, dd, dst, d, dd);
+    note_launch();
     src = dst;
   }
   ABG_LAUNCH_CHECK();
@@ -281,63 +341,96 @@ int orthogonal_matrix(uint64_t seed, int d, double* q, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// CholeskyQR2 of a tall FP32 block Y (M x l): two passes of Gram (FP64, via
+// CholeskyQR2 of tall FP32 blocks per segment: two passes of Gram (FP64, via
 // gemm_tn) -> Cholesky -> Y R^-1 (FP32 GEMM).
 // ---------------------------------------------------------------------------
-int cholqr2(int64_t M, int l, float* Y, int64_t ldy, float* tmp, int64_t ldt, int* breakdowns,
-            Scratch& /*caller*/, cudaStream_t s) {
+int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy, float* tmp,
+            int64_t ldt, int* breakdowns, cudaStream_t s) {
   Scratch scr(s);
-  const int64_t ll = round_up(l, 4);
+  const int64_t ll = round_up(lmax, 4);
+  const int64_t l2 = (int64_t)lmax * lmax;
+  const int nseg = rs.nseg;
   double *Gram, *R, *Ri;
   float* ri32;
-  ABG_TRY(scr.get(&Gram, (size_t)l * l));
-  ABG_TRY(scr.get(&R, (size_t)l * l));
-  ABG_TRY(scr.get(&Ri, (size_t)l * l));
-  ABG_TRY(scr.get(&ri32, (size_t)l * ll));
+  ABG_TRY(scr.get(&Gram, (size_t)nseg * l2));
+  ABG_TRY(scr.get(&R, (size_t)nseg * l2));
+  ABG_TRY(scr.get(&Ri, (size_t)nseg * l2));
+  ABG_TRY(scr.get(&ri32, (size_t)nseg * lmax * ll));
   for (int pass = 0; pass < 2; ++pass) {
     float* src = pass == 0 ? Y : tmp;
     const int64_t lds = pass == 0 ? ldy : ldt;
     float* dst = pass == 0 ? tmp : Y;
     const int64_t ldd = pass == 0 ? ldt : ldy;
-    ABG_TRY(gemm_tn(M, l, l, src, lds, src, lds, Gram, l, scr, s));
-    ABG_TRY(chol_inv(l, Gram, l, R, Ri, ri32, ll, breakdowns, s));
-    ABG_TRY(gemm_nn(M, l, l, src, lds, ri32, ll, dst, ldd, Epi::Store, nullptr, 0, nullptr, 0,
-                    nullptr, s));
+    TN g;
+    g.A = g.B = src;
+    g.lda = g.ldb = lds;
+    g.K = g.N = lmax;
+    g.segK = g.segN = segl;
+    g.C = Gram;
+    g.ldc = lmax;
+    g.c_seg = l2;
+    ABG_TRY(gemm_tn(rs, g, s));
+    // R_s / Ri_s use the segment's own l_s as row stride inside their l2 slabs
+    ABG_TRY(chol_inv(nseg, segl, lmax, Gram, lmax, l2, R, Ri, l2, ri32, ll, lmax * ll, breakdowns,
+                     s));
+    NN a;
+    a.A = src;
+    a.lda = lds;
+    a.B = ri32;
+    a.ldb = ll;
+    a.b_seg = lmax * ll;
+    a.C = dst;
+    a.ldc = ldd;
+    a.N = a.K = lmax;
+    a.segN = a.segK = segl;
+    ABG_TRY(gemm_nn(rs, a, s));
   }
   return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Parallel cyclic Jacobi for a symmetric l x l FP64 matrix (one CTA, round-
-// robin pairing so the l/2 rotations of a step touch disjoint index pairs).
-// A is destroyed; evals (descending) and evecs (columns, l x l) are written.
+// Parallel cyclic Jacobi, one CTA per segment, for the symmetric l_s x l_s FP64
+// matrix A_s (row stride lmax inside a lmax^2 slab; round-robin pairing so the
+// l/2 rotations of a step touch disjoint index pairs). A_s is destroyed;
+// evals_s (descending) and evecs_s (columns, row stride lmax) are written.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ Ag, double* __restrict__ Vg,
+__global__ void __launch_bounds__(1024) k_jacobi(const int* __restrict__ segl, int lmax,
+                                                 double* __restrict__ Aall, double* __restrict__ Vall,
                                                  double* __restrict__ evals,
                                                  double* __restrict__ evecs, int max_sweeps,
                                                  int a_smem, int v_smem) {
   extern __shared__ double js[];
+  const int sg = blockIdx.x;
+  const int l = segl[sg];
+  const int64_t l2 = (int64_t)lmax * lmax;
+  double* Ag = Aall + sg * l2;
+  double* Vg = Vall + sg * l2;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = (l + 1) & ~1;  // even player count (index l is a dummy when l is odd)
   const int P = m / 2;
+  const int Pmax = ((lmax + 1) & ~1) / 2;
   double* cs = js;
-  double* sn = js + P;
-  int* pp = reinterpret_cast<int*>(js + 2 * P);
-  int* qq = pp + P;
-  double* red = js + 3 * P + 1;             // 2 * nt + 1
+  double* sn = js + Pmax;
+  int* pp = reinterpret_cast<int*>(js + 2 * Pmax);
+  int* qq = pp + Pmax;
+  double* red = js + 3 * Pmax + 1;          // 2 * nt + 1
   double* tail = red + 2 * nt + 2;
+  // matrices use row stride l inside shared memory, lmax in global memory
+  const int lda = a_smem ? l : lmax;
+  const int ldv = v_smem ? l : lmax;
   double* A = a_smem ? tail : Ag;
-  double* V = v_smem ? tail + (a_smem ? (int64_t)l * l : 0) : Vg;
+  double* V = v_smem ? tail + (a_smem ? l2 : 0) : Vg;
   if (a_smem)
-    for (int64_t q = tid; q < (int64_t)l * l; q += nt) A[q] = Ag[q];
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt) V[q] = ((q / l) == (q % l)) ? 1.0 : 0.0;
+    for (int64_t q = tid; q < (int64_t)l * l; q += nt) A[q] = Ag[(q / l) * lmax + q % l];
+  for (int64_t q = tid; q < (int64_t)l * l; q += nt)
+    V[(q / l) * ldv + q % l] = ((q / l) == (q % l)) ? 1.0 : 0.0;
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
-      const double v = A[q] * A[q];
-      tot += v;
-      if ((q / l) != (q % l)) off += v;
+      const double v = A[(q / l) * lda + q % l];
+      tot += v * v;
+      if ((q / l) != (q % l)) off += v * v;
     }
     red[tid] = off;
     red[nt + tid] = tot;
@@ -360,9 +453,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ Ag,
         int p = min(a, b), q = max(a, b);
         double c = 1.0, sv = 0.0;
         if (q < l) {
-          const double apq = A[(int64_t)p * l + q];
+          const double apq = A[(int64_t)p * lda + q];
           if (apq != 0.0) {
-            const double app = A[(int64_t)p * l + p], aqq = A[(int64_t)q * l + q];
+            const double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
             const double theta = (aqq - app) / (2.0 * apq);
             const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             c = 1.0 / sqrt(t * t + 1.0);
@@ -375,174 +468,246 @@ __global__ void __launch_bounds__(1024) k_jacobi(int l, double* __restrict__ Ag,
         qq[i] = q;
       }
       __syncthreads();
-      // rows: A <- J^T A (a warp per pair, lanes over columns)
       const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-      for (int i = warp; i < P; i += nw) {
+      for (int i = warp; i < P; i += nw) {  // rows: A <- J^T A
         const int p = pp[i], q = qq[i];
         if (q >= l) continue;
         const double c = cs[i], sv = sn[i];
         for (int k = lane; k < l; k += 32) {
-          const double apk = A[(int64_t)p * l + k], aqk = A[(int64_t)q * l + k];
-          A[(int64_t)p * l + k] = c * apk - sv * aqk;
-          A[(int64_t)q * l + k] = sv * apk + c * aqk;
+          const double apk = A[(int64_t)p * lda + k], aqk = A[(int64_t)q * lda + k];
+          A[(int64_t)p * lda + k] = c * apk - sv * aqk;
+          A[(int64_t)q * lda + k] = sv * apk + c * aqk;
         }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int i = warp; i < P; i += nw) {
+      for (int i = warp; i < P; i += nw) {  // columns: A <- A J, V <- V J
         const int p = pp[i], q = qq[i];
         if (q >= l) continue;
         const double c = cs[i], sv = sn[i];
         for (int k = lane; k < l; k += 32) {
-          const double akp = A[(int64_t)k * l + p], akq = A[(int64_t)k * l + q];
-          A[(int64_t)k * l + p] = c * akp - sv * akq;
-          A[(int64_t)k * l + q] = sv * akp + c * akq;
-          const double vkp = V[(int64_t)k * l + p], vkq = V[(int64_t)k * l + q];
-          V[(int64_t)k * l + p] = c * vkp - sv * vkq;
-          V[(int64_t)k * l + q] = sv * vkp + c * vkq;
+          const double akp = A[(int64_t)k * lda + p], akq = A[(int64_t)k * lda + q];
+          A[(int64_t)k * lda + p] = c * akp - sv * akq;
+          A[(int64_t)k * lda + q] = sv * akp + c * akq;
+          const double vkp = V[(int64_t)k * ldv + p], vkq = V[(int64_t)k * ldv + q];
+          V[(int64_t)k * ldv + p] = c * vkp - sv * vkq;
+          V[(int64_t)k * ldv + q] = sv * vkp + c * vkq;
         }
       }
       __syncthreads();
     }
   }
   // sort descending (rank by value, ties by index) and write eigenpairs
+  double* ev = evals + (int64_t)sg * lmax;
+  double* ec = evecs + sg * l2;
   for (int i = tid; i < l; i += nt) {
-    const double li = A[(int64_t)i * l + i];
+    const double li = A[(int64_t)i * lda + i];
     int rank = 0;
     for (int j = 0; j < l; ++j) {
-      const double lj = A[(int64_t)j * l + j];
+      const double lj = A[(int64_t)j * lda + j];
       rank += (lj > li) || (lj == li && j < i);
     }
-    evals[rank] = li;
-    for (int k = 0; k < l; ++k) evecs[(int64_t)k * l + rank] = V[(int64_t)k * l + i];
+    ev[rank] = li;
+    for (int k = 0; k < l; ++k) ec[(int64_t)k * lmax + rank] = V[(int64_t)k * ldv + i];
   }
 }
 
-static int jacobi_eig(int l, double* A, double* evals, double* evecs, Scratch& /*caller*/, cudaStream_t s) {
+static int jacobi_eig(int nseg, const int* segl, int lmax, double* A, double* evals, double* evecs,
+                      cudaStream_t s) {
   Scratch scr(s);
   double* V;
-  ABG_TRY(scr.get(&V, (size_t)l * l));
+  ABG_TRY(scr.get(&V, (size_t)nseg * lmax * lmax));
   const int threads = 1024;
-  const int P = ((l + 1) & ~1) / 2;
+  const int P = ((lmax + 1) & ~1) / 2;
   const size_t base = sizeof(double) * (3 * P + 1 + 2 * threads + 2);
-  const size_t mat = sizeof(double) * (size_t)l * l;
+  const size_t mat = sizeof(double) * (size_t)lmax * lmax;
   const size_t limit = 220 * 1024;
   const int a_smem = base + mat <= limit;
   const int v_smem = a_smem && base + 2 * mat <= limit;
   const size_t smem = base + (a_smem ? mat : 0) + (v_smem ? mat : 0);
   if (smem > 48 * 1024)
     ABG_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_jacobi<<<1, threads, smem, s>>>(l, A, V, evals, evecs, 40, a_smem, v_smem);
-  ::abg::note_launch();
+  k_jacobi<<<(unsigned)nseg, threads, smem, s>>>(segl, lmax, A, V, evals, evecs, 40, a_smem, v_smem);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Truncated randomized SVD (subspace iteration) and the factors the method
-// needs from it.
+// Truncated randomized SVD per segment
 // ---------------------------------------------------------------------------
-// sign_j = +1 if colsum(Q) . U[:, j] >= 0 else -1 (left vectors summing >= 0);
-// Bm[p][j] = U[p][j] * sign_j * (scale ? sigma_j : 1) for j < k (float, ld ldb)
-__global__ void k_rsvd_post(int l, int k, const double* __restrict__ evals,
+// sign_j = +1 if colsum(Q).U[:, j] >= 0 else -1 (left vectors summing >= 0);
+// Bm_s[p][j] = U_s[p][j] sign_j (x sigma_j in mode 1), Uks_s signed (FP64), sigma_s.
+__global__ void k_rsvd_post(const int* __restrict__ segl, const int* __restrict__ segk, int kfix,
+                            int lmax, int kmax, const double* __restrict__ evals,
                             const double* __restrict__ U, const double* __restrict__ qsum,
                             int with_sigma, float* __restrict__ Bm, int64_t ldb,
-                            double* __restrict__ Uks /* l x k signed, FP64 */,
-                            double* __restrict__ sigma_out) {
+                            double* __restrict__ Uks, double* __restrict__ sigma_out,
+                            int64_t sseg) {
+  const int sg = blockIdx.y;
+  const int l = segl[sg];
+  const int k = segk ? segk[sg] : kfix;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
+  const double* Us = U + (int64_t)sg * lmax * lmax;
+  const double* qs = qsum + (int64_t)sg * lmax;
   double dot = 0.0;
-  for (int p = 0; p < l; ++p) dot += qsum[p] * U[(int64_t)p * l + j];
-  const double sg = dot < 0.0 ? -1.0 : 1.0;
-  const double sigma = sqrt(fmax(evals[j], 0.0));
+  for (int p = 0; p < l; ++p) dot += qs[p] * Us[(int64_t)p * lmax + j];
+  const double sgn = dot < 0.0 ? -1.0 : 1.0;
+  const double sigma = sqrt(fmax(evals[(int64_t)sg * lmax + j], 0.0));
+  float* Bs = Bm + (int64_t)sg * lmax * ldb;
+  double* Uk = Uks + (int64_t)sg * lmax * kmax;
   for (int p = 0; p < l; ++p) {
-    const double u = U[(int64_t)p * l + j] * sg;
-    Uks[(int64_t)p * k + j] = u;
-    Bm[(int64_t)p * ldb + j] = (float)(with_sigma ? u * sigma : u);
+    const double u = Us[(int64_t)p * lmax + j] * sgn;
+    Uk[(int64_t)p * kmax + j] = u;
+    Bs[(int64_t)p * ldb + j] = (float)(with_sigma ? u * sigma : u);
   }
-  if (sigma_out) sigma_out[j] = sigma;
+  if (sigma_out) sigma_out[sg * sseg + j] = sigma;
 }
 
-__global__ void k_relu_f64_to_f32(int rows, int cols, const double* __restrict__ a, int64_t lda,
-                                  float* __restrict__ o, int64_t ldo) {
+__global__ void k_relu_f64_to_f32(int rows, const int* __restrict__ segk, int kmax,
+                                  const double* __restrict__ a, int64_t lda, int64_t aseg,
+                                  float* __restrict__ o, int64_t ldo, int64_t oseg) {
+  const int sg = blockIdx.y;
+  const int k = segk[sg];
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)rows * cols) return;
-  const int i = (int)(q / cols), j = (int)(q % cols);
-  o[(int64_t)i * ldo + j] = (float)fmax(a[(int64_t)i * lda + j], 0.0);
+  if (q >= (int64_t)rows * kmax) return;
+  const int i = (int)(q / kmax), j = (int)(q % kmax);
+  if (j >= k) return;
+  o[sg * oseg + (int64_t)i * ldo + j] = (float)fmax(a[sg * aseg + (int64_t)i * lda + j], 0.0);
 }
 
-// Y (rows x l) = A * Om (dense: gemm_nn; CSR: SpMM)
-static int apply_a(const RsvdIn& in, const float* Om, int64_t ldo, int l, float* Y, int64_t ldy,
-                   cudaStream_t s) {
-  if (in.A)
-    return gemm_nn(in.n, l, in.m, in.A, in.lda, Om, ldo, Y, ldy, Epi::Store, nullptr, 0, nullptr,
-                   0, nullptr, s);
-  return spmm_plain(in.ptr, in.col, in.val, in.n, Om, ldo, l, Y, ldy, s);
+// Y (rows of each segment, l_s columns) = A_s * Om_s
+static int apply_a(const RsvdIn& in, const int* segl, int lmax, const float* Om, int64_t ldo,
+                   float* Y, int64_t ldy, cudaStream_t s) {
+  if (in.A) {
+    NN a;
+    a.A = in.A;
+    a.lda = in.lda;
+    a.B = Om;
+    a.ldb = ldo;
+    a.b_seg = (int64_t)in.m * ldo;
+    a.C = Y;
+    a.ldc = ldy;
+    a.N = lmax;
+    a.K = in.m;
+    a.segN = segl;
+    return gemm_nn(*in.rows, a, s);
+  }
+  // sparse rows gather rows of the stacked test blocks (column s*m + j)
+  return spmm_plain(in.ptr, in.col, in.val, in.rows->rows, Om, ldo, lmax, Y, ldy, s);
 }
 
-// Bt (m x l, FP64) = A^T Q
-static int apply_at(const RsvdIn& in, const float* Q, int64_t ldq, int l, double* Bt, float* tmp32,
-                    int64_t ldt, Scratch& scr, cudaStream_t s) {
-  if (in.A) return gemm_tn(in.n, in.m, l, in.A, in.lda, Q, ldq, Bt, l, scr, s);
-  ABG_TRY(spmm_plain(in.tptr, in.tcol, in.tval, in.m, Q, ldq, l, tmp32, ldt, s));
-  k_f32_to_f64<<<(unsigned)ceil_div((int64_t)in.m * l, 256), 256, 0, s>>>(in.m, l, tmp32, ldt, Bt, l); ::abg::note_launch();
+// Bt_s (m x l_s, FP64, row stride lmax, slab m*lmax) = A_s^T Q_s
+static int apply_at(const RsvdIn& in, const int* segl, int lmax, const float* Q, int64_t ldq,
+                    double* Bt, float* tmp32, int64_t ldt, cudaStream_t s) {
+  const int nseg = in.rows->nseg;
+  if (in.A) {
+    TN t;
+    t.A = in.A;
+    t.lda = in.lda;
+    t.B = Q;
+    t.ldb = ldq;
+    t.K = in.m;
+    t.N = lmax;
+    t.segN = segl;
+    t.C = Bt;
+    t.ldc = lmax;
+    t.c_seg = (int64_t)in.m * lmax;
+    return gemm_tn(*in.rows, t, s);
+  }
+  ABG_TRY(spmm_plain(in.tptr, in.tcol, in.tval, (int64_t)nseg * in.m, Q, ldq, lmax, tmp32, ldt, s));
+  const int64_t rows = (int64_t)nseg * in.m;
+  k_f32_to_f64<<<(unsigned)ceil_div(rows * lmax, 256), 256, 0, s>>>(rows, lmax, tmp32, ldt, Bt, lmax);
+  note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
 }
 
-int rsvd(const RsvdIn& in, int k, int oversample, int power_iters, uint64_t seed, int stream_id,
-         const RsvdOut& out, int* breakdowns, Scratch& /*caller*/, cudaStream_t s) {
-  Scratch scr(s);
-  const int64_t n = in.n;
+int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int stream_id,
+         const RsvdOut& out, int* breakdowns, cudaStream_t s) {
+  const RowSpace& rs = *in.rows;
+  const int nseg = rs.nseg;
   const int m = in.m;
-  const int l = (int)std::min<int64_t>({(int64_t)k + oversample, (int64_t)m, n});
-  ABG_CHECK(k >= 1 && k <= l, "rsvd: need 1 <= k <= min(n, m)");
-  ABG_CHECK(l <= 1024, "rsvd: k + oversample must stay <= 1024");
-  const int64_t ll = round_up(l, 4);
-  float *Om, *Y, *Yt, *T1, *T2, *Bm;
+  const int lmax = ss.l_max;
+  const int kmax = out.left_mode == 0 ? ss.k_max : kfixed;
+  const int* segk = out.left_mode == 0 ? ss.k : nullptr;
+  ABG_CHECK(lmax >= 1 && lmax <= 1024, "rsvd: block width must stay in [1, 1024]");
+  Scratch scr(s);
+  const int64_t ll = round_up(lmax, 4);
+  const int64_t kk = round_up(kmax, 4);
+  const int64_t l2 = (int64_t)lmax * lmax;
+  float *Om, *Y, *T1, *Yt, *T2, *Bm;
   double *Bt, *M, *evals, *evecs, *qsum, *Uks, *Hd;
-  ABG_TRY(scr.get(&Om, (size_t)m * ll));
-  ABG_TRY(scr.get(&Y, (size_t)n * ll));
-  ABG_TRY(scr.get(&T1, (size_t)n * ll));
-  ABG_TRY(scr.get(&Yt, (size_t)m * ll));
-  ABG_TRY(scr.get(&T2, (size_t)m * ll));
-  ABG_TRY(scr.get(&Bt, (size_t)m * l));
-  ABG_TRY(scr.get(&M, (size_t)l * l));
-  ABG_TRY(scr.get(&evals, (size_t)l));
-  ABG_TRY(scr.get(&evecs, (size_t)l * l));
-  ABG_TRY(scr.get(&qsum, (size_t)l));
-  ABG_TRY(scr.get(&Uks, (size_t)l * k));
-  ABG_TRY(scr.get(&Hd, (size_t)m * k));
-  const int64_t kk = round_up(k, 4);
-  ABG_TRY(scr.get(&Bm, (size_t)l * kk));
+  ABG_TRY(scr.get(&Om, (size_t)nseg * m * ll));
+  ABG_TRY(scr.get(&Y, (size_t)rs.rows * ll));
+  ABG_TRY(scr.get(&T1, (size_t)rs.rows * ll));
+  ABG_TRY(scr.get(&Yt, (size_t)nseg * m * ll));
+  ABG_TRY(scr.get(&T2, (size_t)nseg * m * ll));
+  ABG_TRY(scr.get(&Bt, (size_t)nseg * m * lmax));
+  ABG_TRY(scr.get(&M, (size_t)nseg * l2));
+  ABG_TRY(scr.get(&evals, (size_t)nseg * lmax));
+  ABG_TRY(scr.get(&evecs, (size_t)nseg * l2));
+  ABG_TRY(scr.get(&qsum, (size_t)nseg * lmax));
+  ABG_TRY(scr.get(&Uks, (size_t)nseg * lmax * kmax));
+  ABG_TRY(scr.get(&Hd, (size_t)nseg * m * kmax));
+  ABG_TRY(scr.get(&Bm, (size_t)nseg * lmax * kk));
+  RowSpace small;  // m rows per segment (the Omega / A^T Q side)
+  ABG_TRY(rowspace_uniform(&small, nseg, m, scr, s));
   // range finder
-  ABG_TRY(gaussian_f32(seed, stream_id, m, l, Om, ll, s));
-  ABG_TRY(apply_a(in, Om, ll, l, Y, ll, s));
-  ABG_TRY(cholqr2(n, l, Y, ll, T1, ll, breakdowns, scr, s));
+  ABG_TRY(gaussian_f32(nseg, ss.seed, stream_id, m, lmax, ss.l, Om, ll, (int64_t)m * ll, s));
+  ABG_TRY(apply_a(in, ss.l, lmax, Om, ll, Y, ll, s));
+  ABG_TRY(cholqr2(rs, ss.l, lmax, Y, ll, T1, ll, breakdowns, s));
   for (int it = 0; it < power_iters; ++it) {
-    ABG_TRY(apply_at(in, Y, ll, l, Bt, T2, ll, scr, s));
-    k_f64_to_f32<<<(unsigned)ceil_div((int64_t)m * l, 256), 256, 0, s>>>(m, l, Bt, l, Yt, ll, 0); ::abg::note_launch();
-    ABG_LAUNCH_CHECK();
-    ABG_TRY(cholqr2(m, l, Yt, ll, T2, ll, breakdowns, scr, s));
-    ABG_TRY(apply_a(in, Yt, ll, l, Y, ll, s));
-    ABG_TRY(cholqr2(n, l, Y, ll, T1, ll, breakdowns, scr, s));
+    ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
+    ABG_TRY(convert_f64_to_f32(Bt, (int64_t)nseg * m, lmax, lmax, Yt, ll, s));
+    ABG_TRY(cholqr2(small, ss.l, lmax, Yt, ll, T2, ll, breakdowns, s));
+    ABG_TRY(apply_a(in, ss.l, lmax, Yt, ll, Y, ll, s));
+    ABG_TRY(cholqr2(rs, ss.l, lmax, Y, ll, T1, ll, breakdowns, s));
   }
   // B^T = A^T Q (m x l), B B^T = Bt^T Bt (l x l), eigenpairs
-  ABG_TRY(apply_at(in, Y, ll, l, Bt, T2, ll, scr, s));
-  small_tn64(m, l, l, Bt, l, Bt, l, M, l, s);
+  ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
+  {
+    dim3 g((unsigned)ceil_div(l2, 128), (unsigned)nseg);
+    k_small_tn64<<<g, 128, 0, s>>>(m, ss.l, lmax, ss.l, lmax, Bt, lmax, (int64_t)m * lmax, Bt, lmax,
+                                   (int64_t)m * lmax, M, lmax, l2);
+    note_launch();
+  }
   ABG_LAUNCH_CHECK();
-  ABG_TRY(jacobi_eig(l, M, evals, evecs, scr, s));
-  ABG_TRY(column_sums(n, l, Y, ll, qsum, scr, s));
-  k_rsvd_post<<<(unsigned)ceil_div(k, 128), 128, 0, s>>>(l, k, evals, evecs, qsum, out.left_mode,
-                                                         Bm, kk, Uks, out.sigma); ::abg::note_launch();
+  ABG_TRY(jacobi_eig(nseg, ss.l, lmax, M, evals, evecs, s));
+  ABG_TRY(column_sums(rs, lmax, Y, ll, qsum, lmax, s));
+  {
+    dim3 g((unsigned)ceil_div(kmax, 128), (unsigned)nseg);
+    k_rsvd_post<<<g, 128, 0, s>>>(ss.l, segk, kfixed, lmax, kmax, evals, evecs, qsum,
+                                  out.left_mode, Bm, kk, Uks, out.sigma, out.sseg);
+    note_launch();
+  }
   ABG_LAUNCH_CHECK();
   // left factor: Q * (U_k signed [* Sigma]) with max(., 0) for Phi
-  ABG_TRY(gemm_nn(n, k, l, Y, ll, Bm, kk, out.left, out.ldl,
-                  out.left_mode == 0 ? Epi::Relu : Epi::Store, nullptr, 0, nullptr, 0, nullptr, s));
-  if (out.right) {  // H = max(B^T U_k, 0) = max(Psi Sigma, 0)
-    small_nn64(m, l, k, Bt, l, Uks, k, Hd, k, s);
-    k_relu_f64_to_f32<<<(unsigned)ceil_div((int64_t)m * k, 256), 256, 0, s>>>(m, k, Hd, k,
-                                                                             out.right, out.ldr); ::abg::note_launch();
+  {
+    NN a;
+    a.A = Y;
+    a.lda = ll;
+    a.B = Bm;
+    a.ldb = kk;
+    a.b_seg = lmax * kk;
+    a.C = out.left;
+    a.ldc = out.ldl;
+    a.N = kmax;
+    a.K = lmax;
+    a.segN = segk;
+    a.segK = ss.l;
+    a.epi = out.left_mode == 0 ? Epi::Relu : Epi::Store;
+    ABG_TRY(gemm_nn(rs, a, s));
+  }
+  if (out.right) {  // H_s = max(B_s^T U_k, 0) = max(Psi Sigma, 0)
+    dim3 g((unsigned)ceil_div((int64_t)m * kmax, 128), (unsigned)nseg);
+    k_small_nn64<<<g, 128, 0, s>>>(m, ss.l, lmax, segk, kmax, Bt, lmax, (int64_t)m * lmax, Uks,
+                                   kmax, (int64_t)lmax * kmax, Hd, kmax, (int64_t)m * kmax);
+    note_launch();
+    dim3 g2((unsigned)ceil_div((int64_t)m * kmax, 256), (unsigned)nseg);
+    k_relu_f64_to_f32<<<g2, 256, 0, s>>>(m, ss.k, kmax, Hd, kmax, (int64_t)m * kmax, out.right,
+                                         out.ldr, out.rseg);
+    note_launch();
     ABG_LAUNCH_CHECK();
   }
   return ABG_OK;

@@ -1,6 +1,9 @@
-// The whole method (Algorithms 1-3) and the step-level entry points of abg.h.
+// The whole method (Algorithms 1-3 and Eq. 8) over a batch of stacked graphs,
+// the plain single-graph call, the batched call, and the step-level entry
+// points of abg.h (each a one-segment batch).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -16,7 +19,7 @@ struct Ev {
   }
 };
 
-int check_params(const abg_graph* g, const abg_params* p, int* d_eff) {
+int check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d_eff) {
   ABG_CHECK(g && p, "null graph or parameters");
   const int d = p->d == 0 ? g->d_u : p->d;
   ABG_CHECK(d >= 1 && d <= g->d_u, "need 1 <= d <= d_u (got d=%d, d_u=%d)", d, g->d_u);
@@ -24,7 +27,7 @@ int check_params(const abg_graph* g, const abg_params* p, int* d_eff) {
   ABG_CHECK(p->alpha >= 0.0 && p->alpha < 1.0, "need 0 <= alpha < 1");
   ABG_CHECK(p->gamma >= 0 && p->t_f >= 0 && p->t_g >= 0, "gamma, t_f, t_g must be >= 0");
   ABG_CHECK(p->oversample >= 0 && p->power_iters >= 0, "oversample, power_iters must be >= 0");
-  ABG_CHECK(p->k >= 1 && p->k <= kMaxK && p->k <= 2 * d && p->k <= g->n_u,
+  ABG_CHECK(p->k >= 1 && p->k <= kMaxK && p->k <= 2 * d && p->k <= n_rows,
             "need 1 <= k <= min(|U|, 2d, %d) (got k=%d)", kMaxK, p->k);
   ABG_CHECK(d == g->d_u || (int64_t)d + p->oversample <= 1024,
             "attribute reduction needs d + oversample <= 1024");
@@ -32,11 +35,21 @@ int check_params(const abg_graph* g, const abg_params* p, int* d_eff) {
   return ABG_OK;
 }
 
-// Attributes the propagation reads: the graph's own (dense), a densified CSR,
-// or the SVD-reduced X' of Eq. 15.
-int prepare_attributes(const abg_graph* g, int d, int oversample, int power_iters, uint64_t seed,
-                       Scratch& scr, cudaStream_t s, const float** xf, const __nv_bfloat16** xb,
-                       int64_t* ldx, int* breakdowns) {
+// Device outputs of one batched solve.
+struct SolveOut {
+  int32_t* labels = nullptr;   // rows
+  double* obj = nullptr;       // 2 per segment
+  int* counters = nullptr;     // 3 per segment: changes, min margin bits, empty clusters
+  int* clamped = nullptr;      // per segment
+  int* breakdowns = nullptr;   // 1
+};
+
+// Attributes the propagation reads: the graph's own (dense), a densified CSR, or the
+// per-segment SVD-reduced X' of Eq. 15.
+int prepare_attributes(const abg_graph* g, const RowSpace& rs, int d, int oversample,
+                       int power_iters, const std::vector<uint64_t>& seeds, Scratch& scr,
+                       cudaStream_t s, const float** xf, const __nv_bfloat16** xb, int64_t* ldx,
+                       int* breakdowns) {
   *xf = nullptr;
   *xb = nullptr;
   if (d == g->d_u) {
@@ -59,12 +72,19 @@ int prepare_attributes(const abg_graph* g, int d, int oversample, int power_iter
   const int64_t ldo = round_up(d, 4);
   float* xr;
   ABG_TRY(scr.get(&xr, (size_t)g->n_u * ldo));
+  std::vector<int> kx(rs.nseg, d), lx(rs.nseg);
+  for (int i = 0; i < rs.nseg; ++i)
+    lx[i] = (int)std::min<int64_t>({(int64_t)d + oversample, (int64_t)g->d_u, rs.h_n[i]});
+  for (int i = 0; i < rs.nseg; ++i)
+    ABG_CHECK(lx[i] >= d, "attribute reduction of segment %d: d exceeds its row count", i);
+  SegSizes ssx;
+  ABG_TRY(segsizes_build(&ssx, kx, lx, seeds, scr, s));
   RsvdIn in;
-  in.n = g->n_u;
+  in.rows = &rs;
   in.m = g->d_u;
   if (g->x_kind == ABG_X_CSR_F32) {
     in.ptr = g->x_ptr;
-    in.col = g->x_col;
+    in.col = g->xr_col;
     in.val = g->x_val;
     in.tptr = g->xt_ptr;
     in.tcol = g->xt_col;
@@ -83,42 +103,256 @@ int prepare_attributes(const abg_graph* g, int d, int oversample, int power_iter
   out.left = xr;
   out.ldl = ldo;
   out.left_mode = 1;
-  ABG_TRY(rsvd(in, d, oversample, power_iters, seed, ABG_STREAM_OMEGA_X, out, breakdowns, scr, s));
+  ABG_TRY(rsvd(in, ssx, d, power_iters, ABG_STREAM_OMEGA_X, out, breakdowns, s));
   *xf = xr;
   *ldx = ldo;
   return ABG_OK;
 }
 
-int onmf_iterations(const float* R, int64_t n, int m, int64_t ldr, int k, int t_f, float* phi,
-                    int64_t ldphi, float* H, int64_t ldh, Scratch& scr, cudaStream_t s) {
+int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int64_t ldr,
+                    int t_f, float* phi, int64_t ldphi, float* H, int64_t ldh, int64_t hseg,
+                    cudaStream_t s) {
   if (t_f == 0) return ABG_OK;
+  const int nseg = rs.nseg, kmax = ss.k_max;
+  const int64_t kk = round_up(kmax, 4);
+  Scratch scr(s);
   float *P, *phi2, *C32;
   double *A, *G, *C;
-  ABG_TRY(scr.get(&P, (size_t)n * ldphi));
-  ABG_TRY(scr.get(&phi2, (size_t)n * ldphi));
-  ABG_TRY(scr.get(&C32, (size_t)k * ldphi));
-  ABG_TRY(scr.get(&A, (size_t)m * k));
-  ABG_TRY(scr.get(&G, (size_t)k * k));
-  ABG_TRY(scr.get(&C, (size_t)k * k));
+  ABG_TRY(scr.get(&P, (size_t)rs.rows * ldphi));
+  ABG_TRY(scr.get(&phi2, (size_t)rs.rows * ldphi));
+  ABG_TRY(scr.get(&C32, (size_t)nseg * kmax * kk));
+  ABG_TRY(scr.get(&A, (size_t)nseg * m * kmax));
+  ABG_TRY(scr.get(&G, (size_t)nseg * kmax * kmax));
+  ABG_TRY(scr.get(&C, (size_t)nseg * kmax * kmax));
   float* cur = phi;
   float* nxt = phi2;
   for (int t = 0; t < t_f; ++t) {
     // Eq. 16: H <- H * (R^T Phi) / (H (Phi^T Phi))
-    ABG_TRY(gemm_tn(n, m, k, R, ldr, cur, ldphi, A, k, scr, s));
-    ABG_TRY(gemm_tn(n, k, k, cur, ldphi, cur, ldphi, G, k, scr, s));
-    ABG_TRY(nmf_update_h(m, k, H, ldh, A, k, G, k, s));
+    TN ta;
+    ta.A = R;
+    ta.lda = ldr;
+    ta.B = cur;
+    ta.ldb = ldphi;
+    ta.K = m;
+    ta.N = kmax;
+    ta.segN = ss.k;
+    ta.C = A;
+    ta.ldc = kmax;
+    ta.c_seg = (int64_t)m * kmax;
+    ABG_TRY(gemm_tn(rs, ta, s));
+    TN tg;
+    tg.A = tg.B = cur;
+    tg.lda = tg.ldb = ldphi;
+    tg.K = tg.N = kmax;
+    tg.segK = tg.segN = ss.k;
+    tg.C = G;
+    tg.ldc = kmax;
+    tg.c_seg = (int64_t)kmax * kmax;
+    ABG_TRY(gemm_tn(rs, tg, s));
+    ABG_TRY(nmf_update_h(nseg, m, ss.k, kmax, H, ldh, hseg, A, kmax, (int64_t)m * kmax, G, kmax,
+                         (int64_t)kmax * kmax, s));
     // Eq. 17: Phi <- Phi * sqrt((R H) / (Phi (Phi^T (R H))))
-    ABG_TRY(gemm_nn(n, k, m, R, ldr, H, ldh, P, ldphi, Epi::Store, nullptr, 0, nullptr, 0, nullptr,
-                    s));
-    ABG_TRY(gemm_tn(n, k, k, cur, ldphi, P, ldphi, C, k, scr, s));
-    ABG_TRY(convert_f64_to_f32(C, k, k, k, C32, ldphi, s));
-    ABG_TRY(gemm_nn(n, k, k, cur, ldphi, C32, ldphi, nxt, ldphi, Epi::PhiUpdate, P, ldphi, cur,
-                    ldphi, nullptr, s));
+    NN pr;
+    pr.A = R;
+    pr.lda = ldr;
+    pr.B = H;
+    pr.ldb = ldh;
+    pr.b_seg = hseg;
+    pr.C = P;
+    pr.ldc = ldphi;
+    pr.N = kmax;
+    pr.K = m;
+    pr.segN = ss.k;
+    ABG_TRY(gemm_nn(rs, pr, s));
+    TN tc;
+    tc.A = cur;
+    tc.lda = ldphi;
+    tc.B = P;
+    tc.ldb = ldphi;
+    tc.K = tc.N = kmax;
+    tc.segK = tc.segN = ss.k;
+    tc.C = C;
+    tc.ldc = kmax;
+    tc.c_seg = (int64_t)kmax * kmax;
+    ABG_TRY(gemm_tn(rs, tc, s));
+    ABG_TRY(convert_f64_to_f32(C, (int64_t)nseg * kmax, kmax, kmax, C32, kk, s));
+    NN pu;
+    pu.A = cur;
+    pu.lda = ldphi;
+    pu.B = C32;
+    pu.ldb = kk;
+    pu.b_seg = (int64_t)kmax * kk;
+    pu.C = nxt;
+    pu.ldc = ldphi;
+    pu.N = pu.K = kmax;
+    pu.segN = pu.segK = ss.k;
+    pu.epi = Epi::PhiUpdate;
+    pu.aux = P;
+    pu.ldaux = ldphi;
+    pu.aux2 = cur;
+    pu.ldaux2 = ldphi;
+    ABG_TRY(gemm_nn(rs, pu, s));
     std::swap(cur, nxt);
   }
   if (cur != phi)
-    ABG_CUDA(cudaMemcpyAsync(phi, cur, sizeof(float) * n * ldphi, cudaMemcpyDeviceToDevice, s));
+    ABG_CUDA(cudaMemcpyAsync(phi, cur, sizeof(float) * rs.rows * ldphi, cudaMemcpyDeviceToDevice, s));
   return ABG_OK;
+}
+
+// Algorithms 1-3 and Eq. 8 for every segment of g; ev[0..6] (optional) get the phase
+// boundaries recorded on s.
+int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& ks,
+                const std::vector<uint64_t>& seeds, const abg_params& p, int d, SolveOut& o,
+                cudaEvent_t* ev, cudaStream_t s) {
+  const int nseg = rs.nseg;
+  const int64_t n = g->n_u;
+  const int m = 2 * d;
+  Scratch scr(s);
+  // per-segment sizes first: building them waits for their upload
+  std::vector<int> ls(nseg);
+  for (int i = 0; i < nseg; ++i)
+    ls[i] = (int)std::min<int64_t>({(int64_t)ks[i] + p.oversample, (int64_t)m, rs.h_n[i]});
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, ks, ls, seeds, scr, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[0], s));
+  // ---- Algorithm 1 ----
+  const float* xf;
+  const __nv_bfloat16* xb;
+  int64_t ldx;
+  ABG_TRY(prepare_attributes(g, rs, d, p.oversample, p.power_iters, seeds, scr, s, &xf, &xb, &ldx,
+                             o.breakdowns));
+  const int64_t ldz = round_up(d, 4);
+  float* zhat;
+  ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[1], s));
+  ABG_TRY(propagate(g, xf, xb, ldx, d, p.alpha, p.gamma, zhat, ldz, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[2], s));
+  double* q;
+  float* qt;
+  ABG_TRY(scr.get(&q, (size_t)nseg * d * d));
+  ABG_TRY(scr.get(&qt, (size_t)nseg * d * ldz));
+  ABG_TRY(orthogonal_matrices(nseg, ss.seed, d, q, s));
+  ABG_TRY(transpose_blocks(nseg, d, q, qt, ldz, s));
+  const int64_t ldr = round_up(m, 4);
+  float* R;
+  ABG_TRY(scr.get(&R, (size_t)n * ldr));
+  ABG_TRY(random_features(rs, zhat, d, ldz, qt, ldz, R, ldr, o.clamped, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[3], s));
+  // ---- Algorithm 2 ----
+  const int kmax = ss.k_max;
+  const int64_t kk = round_up(kmax, 4);
+  const int64_t hseg = (int64_t)m * kk;
+  float *phi, *H;
+  ABG_TRY(scr.get(&phi, (size_t)n * kk));
+  ABG_TRY(scr.get(&H, (size_t)nseg * hseg));
+  RsvdIn in;
+  in.rows = &rs;
+  in.m = m;
+  in.A = R;
+  in.lda = ldr;
+  RsvdOut out;
+  out.left = phi;
+  out.ldl = kk;
+  out.left_mode = 0;
+  out.right = H;
+  out.ldr = kk;
+  out.rseg = hseg;
+  ABG_TRY(rsvd(in, ss, 0, p.power_iters, ABG_STREAM_OMEGA_R, out, o.breakdowns, s));
+  ABG_TRY(onmf_iterations(rs, ss, R, m, ldr, p.t_f, phi, kk, H, kk, hseg, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[4], s));
+  // ---- Algorithm 3 ----
+  ABG_TRY(nci_run(rs, ss, phi, kk, p.t_g, o.labels, nullptr, nullptr, o.counters, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[5], s));
+  // ---- Eq. 8 ----
+  ABG_TRY(objective(rs, ss, R, m, ldr, o.labels, o.obj, s));
+  if (ev) ABG_CUDA(cudaEventRecord(ev[6], s));
+  return ABG_OK;
+}
+
+int rowspace_of(const abg_graph* g, RowSpace* rs, Scratch& scr, cudaStream_t s) {
+  return rowspace_build(rs, g->seg_row0, g->seg_n, scr, s);
+}
+
+// Run the batched solve of g (one parameter set per segment) and bring results to the host.
+int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int32_t* labels,
+                 abg_result* res) {
+  ABG_CHECK(g && ps && labels, "null argument");
+  ABG_CHECK(np == g->nseg, "need one parameter set per segment (%d given, %d segments)", np, g->nseg);
+  int d = 0;
+  for (int i = 0; i < np; ++i) {
+    int di = 0;
+    ABG_TRY(check_params(g, &ps[i], g->seg_n[i], &di));
+    if (i == 0) d = di;
+    ABG_CHECK(di == d && ps[i].alpha == ps[0].alpha && ps[i].gamma == ps[0].gamma &&
+                  ps[i].t_f == ps[0].t_f && ps[i].t_g == ps[0].t_g &&
+                  ps[i].oversample == ps[0].oversample && ps[i].power_iters == ps[0].power_iters,
+              "batched solves need the same d, alpha, gamma, t_f, t_g, oversample, power_iters");
+  }
+  ABG_CUDA(cudaSetDevice(g->device));
+  const int nseg = g->nseg;
+  std::vector<int> ks(nseg);
+  std::vector<uint64_t> seeds(nseg);
+  for (int i = 0; i < nseg; ++i) {
+    ks[i] = ps[i].k;
+    seeds[i] = ps[i].seed;
+  }
+  Ev e[7];
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) ev[i] = e[i].e;
+  std::vector<double> obj(2 * nseg);
+  std::vector<int> cnt(3 * nseg), cl(nseg);
+  int bd = 0;
+  {
+    Scratch scr(s);
+    RowSpace rs;
+    ABG_TRY(rowspace_of(g, &rs, scr, s));
+    SolveOut o;
+    ABG_TRY(scr.get(&o.labels, (size_t)g->n_u));
+    ABG_TRY(scr.get(&o.obj, (size_t)2 * nseg));
+    ABG_TRY(scr.get(&o.counters, (size_t)3 * nseg));
+    ABG_TRY(scr.get(&o.clamped, (size_t)nseg));
+    ABG_TRY(scr.get(&o.breakdowns, 1));
+    ABG_CUDA(cudaMemsetAsync(o.clamped, 0, sizeof(int) * nseg, s));
+    ABG_CUDA(cudaMemsetAsync(o.breakdowns, 0, sizeof(int), s));
+    ABG_TRY(solve_batch(g, rs, ks, seeds, ps[0], d, o, ev, s));
+    ABG_CUDA(cudaMemcpyAsync(labels, o.labels, sizeof(int32_t) * g->n_u, cudaMemcpyDefault, s));
+    ABG_CUDA(cudaMemcpyAsync(obj.data(), o.obj, sizeof(double) * 2 * nseg, cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaMemcpyAsync(cnt.data(), o.counters, sizeof(int) * 3 * nseg, cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaMemcpyAsync(cl.data(), o.clamped, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaMemcpyAsync(&bd, o.breakdowns, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaStreamSynchronize(s));
+  }
+  ABG_CUDA(cudaStreamSynchronize(s));
+  ABG_CUDA(cudaGetLastError());
+  float ms[6];
+  for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  bool finite = true;
+  for (int i = 0; i < nseg; ++i) {
+    abg_result r{};
+    r.objective = obj[2 * i];
+    r.trace_obj = obj[2 * i + 1];
+    r.last_changes = ps[i].t_g > 0 ? cnt[i] : 0;
+    unsigned b = (unsigned)cnt[nseg + i];
+    float f;
+    memcpy(&f, &b, sizeof(f));
+    r.min_margin = ps[i].t_g > 0 ? f : INFINITY;
+    r.empty_clusters = ps[i].t_g > 0 ? cnt[2 * nseg + i] : ps[i].k - 1;
+    r.clamped_rows = cl[i];
+    r.chol_breakdowns = bd;
+    for (int j = 0; j < 6; ++j) r.ms_phase[j] = ms[j];
+    finite &= std::isfinite(r.objective);
+    if (res) res[i] = r;
+  }
+  if (!finite) {
+    set_error("objective is not finite");
+    return ABG_ENUMERIC;
+  }
+  return ABG_OK;
+}
+
+// One-segment row space over n rows.
+int single_rows(int64_t n, RowSpace* rs, Scratch& scr, cudaStream_t s) {
+  return rowspace_build(rs, std::vector<int64_t>{0}, std::vector<int64_t>{n}, scr, s);
 }
 
 }  // namespace
@@ -141,7 +375,7 @@ ABG_API void abg_params_default(abg_params* p) {
 
 ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
   int d = 0;
-  if (!g || !p || check_params(g, p, &d) != ABG_OK) return -1;
+  if (!g || !p || check_params(g, p, g->n_u, &d) != ABG_OK) return -1;
   const int64_t n = g->n_u;
   const int64_t ld = round_up(d, 4), ldr = round_up(2 * d, 4), kk = round_up(p->k, 4);
   const int64_t l = std::min<int64_t>(p->k + p->oversample, 2 * d);
@@ -152,8 +386,8 @@ ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
   b += 4 * n * ldr;                      // R
   b += 4 * n * ll * 2;                   // randomized SVD blocks
   b += 4 * n * kk * 4;                   // Phi (x2), P, spare
-  b += 8 * n;                            // labels
-  b += 4 * (ceil_div(n, 2048) + 1) * (int64_t)std::max(2 * d, 128) * 128;  // chunk partials
+  b += 8 * n;                            // labels, row segments
+  b += 4 * (ceil_div(n, 2048) + g->nseg) * std::max<int64_t>(2 * d, 128) * std::max<int64_t>(kk, ll);
   if (d < g->d_u) b += 4 * n * (ld + round_up(d + p->oversample, 4) * 2 + g->ldx);
   else if (g->x_kind == ABG_X_CSR_F32) b += 4 * n * ld;
   return b + (64 << 20);
@@ -161,96 +395,18 @@ ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
 
 ABG_API int abg_cluster(abg_graph* g, const abg_params* p, void* stream, int32_t* labels,
                         abg_result* res) {
-  int d = 0;
-  ABG_TRY(check_params(g, p, &d));
-  ABG_CHECK(labels, "null labels buffer");
-  ABG_CUDA(cudaSetDevice(g->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  const int64_t n = g->n_u;
-  const int k = p->k;
-  Ev e0, e1, e2, e3, e4, e5, e6;
-  int* bd;
-  abg_result r{};
-  {
-    Scratch scr(s);
-    ABG_TRY(scr.get(&bd, 1));
-    ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
-    ABG_CUDA(cudaEventRecord(e0.e, s));
-    // ---- Algorithm 1 ----
-    const float* xf;
-    const __nv_bfloat16* xb;
-    int64_t ldx;
-    ABG_TRY(prepare_attributes(g, d, p->oversample, p->power_iters, p->seed, scr, s, &xf, &xb, &ldx,
-                               bd));
-    const int64_t ldz = round_up(d, 4);
-    float* zhat;
-    ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
-    ABG_CUDA(cudaEventRecord(e1.e, s));
-    ABG_TRY(propagate(g, xf, xb, ldx, d, p->alpha, p->gamma, zhat, ldz, s));
-    ABG_CUDA(cudaEventRecord(e2.e, s));
-    double* q;
-    float* qt;
-    ABG_TRY(scr.get(&q, (size_t)d * d));
-    ABG_TRY(scr.get(&qt, (size_t)d * ldz));
-    ABG_TRY(orthogonal_matrix(p->seed, d, q, s));
-    ABG_TRY(transpose_f64_to_f32(q, d, d, d, qt, ldz, s));
-    const int m = 2 * d;
-    const int64_t ldr = round_up(m, 4);
-    float* R;
-    ABG_TRY(scr.get(&R, (size_t)n * ldr));
-    int* clamped;
-    ABG_TRY(scr.get(&clamped, 1));
-    ABG_CUDA(cudaMemsetAsync(clamped, 0, sizeof(int), s));
-    ABG_TRY(random_features(zhat, n, d, ldz, qt, R, ldr, clamped, scr, s));
-    ABG_CUDA(cudaEventRecord(e3.e, s));
-    // ---- Algorithm 2 ----
-    const int64_t kk = round_up(k, 4);
-    float *phi, *H;
-    ABG_TRY(scr.get(&phi, (size_t)n * kk));
-    ABG_TRY(scr.get(&H, (size_t)m * kk));
-    RsvdIn in;
-    in.n = n;
-    in.m = m;
-    in.A = R;
-    in.lda = ldr;
-    RsvdOut out;
-    out.left = phi;
-    out.ldl = kk;
-    out.left_mode = 0;
-    out.right = H;
-    out.ldr = kk;
-    ABG_TRY(rsvd(in, k, p->oversample, p->power_iters, p->seed, ABG_STREAM_OMEGA_R, out, bd, scr, s));
-    ABG_TRY(onmf_iterations(R, n, m, ldr, k, p->t_f, phi, kk, H, kk, scr, s));
-    ABG_CUDA(cudaEventRecord(e4.e, s));
-    // ---- Algorithm 3 ----
-    int32_t* lab;
-    ABG_TRY(scr.get(&lab, (size_t)n));
-    float minm = INFINITY;
-    ABG_TRY(nci_run(phi, n, k, kk, p->t_g, lab, nullptr, nullptr, &r.last_changes, &minm,
-                    &r.empty_clusters, scr, s));
-    r.min_margin = minm;
-    ABG_CUDA(cudaEventRecord(e5.e, s));
-    // ---- Eq. 8 ----
-    double obj[2] = {0, 0};
-    ABG_TRY(objective(R, n, m, ldr, lab, k, obj, scr, s));
-    r.objective = obj[0];
-    r.trace_obj = obj[1];
-    ABG_CUDA(cudaEventRecord(e6.e, s));
-    ABG_CUDA(cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDefault, s));
-    ABG_CUDA(cudaMemcpyAsync(&r.chol_breakdowns, bd, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ABG_CUDA(cudaMemcpyAsync(&r.clamped_rows, clamped, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ABG_CHECK(g, "null graph");
+  if (g->nseg != 1) {
+    set_error("abg_cluster on a batch: use abg_batch_cluster (one parameter set per graph)");
+    return ABG_EINVAL;
   }
-  ABG_CUDA(cudaStreamSynchronize(s));
-  ABG_CUDA(cudaGetLastError());
-  cudaEvent_t ev[7] = {e0.e, e1.e, e2.e, e3.e, e4.e, e5.e, e6.e};
-  for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&r.ms_phase[i], ev[i], ev[i + 1]);
-  if (!std::isfinite(r.objective)) {
-    set_error("objective is not finite");
-    if (res) *res = r;
-    return ABG_ENUMERIC;
-  }
-  if (res) *res = r;
-  return ABG_OK;
+  return cluster_impl(g, p, 1, (cudaStream_t)stream, labels, res);
+}
+
+ABG_API int abg_batch_cluster(abg_graph* batch, const abg_params* params, void* stream,
+                              int32_t* labels, abg_result* results) {
+  ABG_CHECK(batch, "null batch");
+  return cluster_impl(batch, params, batch->nseg, (cudaStream_t)stream, labels, results);
 }
 
 ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversample,
@@ -263,13 +419,16 @@ ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversam
   ABG_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
+  RowSpace rs;
+  ABG_TRY(rowspace_of(g, &rs, scr, s));
   int* bd;
   ABG_TRY(scr.get(&bd, 1));
   ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
   const float* xf;
   const __nv_bfloat16* xb;
   int64_t ldx;
-  ABG_TRY(prepare_attributes(g, d, oversample, power_iters, seed, scr, s, &xf, &xb, &ldx, bd));
+  std::vector<uint64_t> seeds(g->nseg, seed);
+  ABG_TRY(prepare_attributes(g, rs, d, oversample, power_iters, seeds, scr, s, &xf, &xb, &ldx, bd));
   ABG_CUDA(cudaMemcpy2DAsync(x_out, sizeof(float) * ldo, xf, sizeof(float) * ldx, sizeof(float) * d,
                              g->n_u, cudaMemcpyDeviceToDevice, s));
   return ABG_OK;
@@ -283,16 +442,23 @@ ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32
   if (x) return propagate(g, x, nullptr, ldx, d, alpha, gamma, zhat, ldz, s);
   ABG_CHECK(d == g->d_u, "x = NULL needs d == d_u");
   Scratch scr(s);
+  RowSpace rs;
+  ABG_TRY(rowspace_of(g, &rs, scr, s));
   const float* xf;
   const __nv_bfloat16* xb;
   int64_t lx;
-  ABG_TRY(prepare_attributes(g, d, 0, 0, 0, scr, s, &xf, &xb, &lx, nullptr));
+  std::vector<uint64_t> seeds(g->nseg, 0);
+  ABG_TRY(prepare_attributes(g, rs, d, 0, 0, seeds, scr, s, &xf, &xb, &lx, nullptr));
   return propagate(g, xf, xb, lx, d, alpha, gamma, zhat, ldz, s);
 }
 
 ABG_API int abg_orthogonal_matrix(uint64_t seed, int32_t d, double* q_out, void* stream) {
   ABG_CHECK(q_out, "null output");
-  return orthogonal_matrix(seed, d, q_out, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch scr(s);
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {1}, {1}, {seed}, scr, s));
+  return orthogonal_matrices(1, ss.seed, d, q_out, s);
 }
 
 ABG_API int abg_random_features(const float* zhat, int64_t n, int32_t d, int64_t ldz, uint64_t seed,
@@ -301,17 +467,21 @@ ABG_API int abg_random_features(const float* zhat, int64_t n, int32_t d, int64_t
   ABG_CHECK(ldz >= d && ldz % 4 == 0, "ldz must be >= d and a multiple of 4");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
+  RowSpace rs;
+  ABG_TRY(single_rows(n, &rs, scr, s));
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {1}, {1}, {seed}, scr, s));
   double* q;
   float* qt;
   const int64_t ldq = round_up(d, 4);
   ABG_TRY(scr.get(&q, (size_t)d * d));
   ABG_TRY(scr.get(&qt, (size_t)d * ldq));
-  ABG_TRY(orthogonal_matrix(seed, d, q, s));
-  ABG_TRY(transpose_f64_to_f32(q, d, d, d, qt, ldq, s));
+  ABG_TRY(orthogonal_matrices(1, ss.seed, d, q, s));
+  ABG_TRY(transpose_blocks(1, d, q, qt, ldq, s));
   int* cl;
   ABG_TRY(scr.get(&cl, 1));
   ABG_CUDA(cudaMemsetAsync(cl, 0, sizeof(int), s));
-  ABG_TRY(random_features(zhat, n, d, ldz, qt, r_out, ldr, cl, scr, s));
+  ABG_TRY(random_features(rs, zhat, d, ldz, qt, ldq, r_out, ldr, cl, s));
   if (clamped) {
     ABG_CUDA(cudaMemcpyAsync(clamped, cl, sizeof(int), cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaStreamSynchronize(s));
@@ -330,11 +500,16 @@ ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, 
   ABG_CHECK(oversample >= 0 && power_iters >= 0 && k + oversample <= 1024, "bad SVD parameters");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
+  RowSpace rs;
+  ABG_TRY(single_rows(n, &rs, scr, s));
+  const int l = (int)std::min<int64_t>({(int64_t)k + oversample, (int64_t)m, n});
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {k}, {l}, {seed}, scr, s));
   int* bd;
   ABG_TRY(scr.get(&bd, 1));
   ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
   RsvdIn in;
-  in.n = n;
+  in.rows = &rs;
   in.m = m;
   in.A = r;
   in.lda = ldr;
@@ -345,7 +520,7 @@ ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, 
   out.right = h_out;
   out.ldr = ldh;
   out.sigma = sigma_out;
-  return rsvd(in, k, oversample, power_iters, seed, ABG_STREAM_OMEGA_R, out, bd, scr, s);
+  return rsvd(in, ss, 0, power_iters, ABG_STREAM_OMEGA_R, out, bd, s);
 }
 
 ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k, int32_t t_f,
@@ -355,30 +530,50 @@ ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t 
             "leading dimensions must cover the width and be multiples of 4");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
-  return onmf_iterations(r, n, m, ldr, k, t_f, phi, ldphi, h, ldh, scr, s);
+  RowSpace rs;
+  ABG_TRY(single_rows(n, &rs, scr, s));
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {k}, {k}, {0}, scr, s));
+  return onmf_iterations(rs, ss, r, m, ldr, t_f, phi, ldphi, h, ldh, (int64_t)m * ldh, s);
 }
 
 ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32_t t_g,
                     int32_t* labels_out, float* margin_out, double* t_out, int32_t* last_changes,
                     void* stream) {
-  ABG_CHECK(phi && labels_out && n >= 1 && t_g >= 0, "bad arguments");
+  ABG_CHECK(phi && labels_out && n >= 1 && t_g >= 0 && k >= 1 && k <= kMaxK, "bad arguments");
   ABG_CHECK(ldphi >= k && ldphi % 4 == 0, "ldphi must be >= k and a multiple of 4");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
-  int lc = 0;
-  ABG_TRY(nci_run(phi, n, k, ldphi, t_g, labels_out, margin_out, t_out, &lc, nullptr, nullptr, scr,
-                  s));
-  if (last_changes) *last_changes = lc;
+  RowSpace rs;
+  ABG_TRY(single_rows(n, &rs, scr, s));
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {k}, {k}, {0}, scr, s));
+  int* counters;
+  ABG_TRY(scr.get(&counters, 3));
+  ABG_TRY(nci_run(rs, ss, phi, ldphi, t_g, labels_out, margin_out, t_out, counters, s));
+  int host[3] = {0, 0, 0};
+  ABG_CUDA(cudaMemcpyAsync(host, counters, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  if (last_changes) *last_changes = t_g > 0 ? host[0] : 0;
   return ABG_OK;
 }
 
 ABG_API int abg_objective(const float* r, int64_t n, int32_t m, int64_t ldr, const int32_t* labels,
                           int32_t k, double* obj, void* stream) {
-  ABG_CHECK(r && labels && obj && n >= 1 && m >= 1, "bad arguments");
+  ABG_CHECK(r && labels && obj && n >= 1 && m >= 1 && k >= 1 && k <= kMaxK, "bad arguments");
   ABG_CHECK(ldr >= m && ldr % 4 == 0, "ldr must be >= m and a multiple of 4");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch scr(s);
-  return objective(r, n, m, ldr, labels, k, obj, scr, s);
+  RowSpace rs;
+  ABG_TRY(single_rows(n, &rs, scr, s));
+  SegSizes ss;
+  ABG_TRY(segsizes_build(&ss, {k}, {k}, {0}, scr, s));
+  double* out;
+  ABG_TRY(scr.get(&out, 2));
+  ABG_TRY(objective(rs, ss, r, m, ldr, labels, out, s));
+  ABG_CUDA(cudaMemcpyAsync(obj, out, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  return ABG_OK;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ struct EpiParams {
   const void* x;     // restart attributes (float or bf16), row stride ldx
   int x_bf16;
   int64_t ldx;
+  int d;             // row width: components at or beyond d are treated as 0 and written as 0
 };
 
 template <class T>
@@ -90,10 +91,23 @@ __device__ __forceinline__ void gather_range(int64_t b, int64_t e, const int32_t
   }
 }
 
+// zero the components of chunk ch that lie at or beyond column d (row padding)
+__device__ __forceinline__ float4 mask_tail(float4 v, int ch, int d) {
+  const int c0 = 4 * ch;
+  if (c0 + 1 >= d) v.y = 0.f;
+  if (c0 + 2 >= d) v.z = 0.f;
+  if (c0 + 3 >= d) v.w = 0.f;
+  if (c0 >= d) v.x = 0.f;
+  return v;
+}
+
 template <int G, int V>
-__device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc)[V], float* C,
+__device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc_in)[V], float* C,
                                                int64_t ldc, int nchunk, int lig, unsigned mask,
                                                const EpiParams& ep) {
+  float4 acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = mask_tail(acc_in[v], lig + G * v, ep.d);
   float4 out[V];
   if (ep.mode == 0) {
 #pragma unroll
@@ -111,6 +125,7 @@ __device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc)[
           xv = ld_bf16x4(reinterpret_cast<const __nv_bfloat16*>(ep.x) + row * ep.ldx + 4 * ch);
         else
           xv = ld_nc_f4(reinterpret_cast<const float*>(ep.x) + row * ep.ldx + 4 * ch);
+        xv = mask_tail(xv, ch, ep.d);
       }
       float4 z;
       z.x = fmaf(ep.c_p, acc[v].x, ep.c_x * xv.x);
@@ -321,7 +336,7 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
             "propagate: leading dimensions must be >= d and multiples of 4");
   const int nchunk = (d + 3) / 4;
   EpiParams ep_restart{1, 1.f, (float)(1.0 - alpha), (float)alpha,
-                       x_f32 ? (const void*)x_f32 : (const void*)x_bf16, x_bf16 != nullptr, ldx};
+                       x_f32 ? (const void*)x_f32 : (const void*)x_bf16, x_bf16 != nullptr, ldx, d};
   if (gamma == 0) {
     EpiParams ep = ep_restart;
     ep.mode = 2;
@@ -337,7 +352,7 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
   for (int it = 0; it < gamma; ++it) {
     // W = L^T Z   (Z_0 = (1-a) X gathered straight from the attributes)
     if (it == 0) {
-      EpiParams ep{0, (float)(1.0 - alpha), 0.f, 0.f, nullptr, 0, 0};
+      EpiParams ep{0, (float)(1.0 - alpha), 0.f, 0.f, nullptr, 0, 0, d};
       if (x_bf16)
         ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, g->sched_v.light, g->sched_v.n_light,
                                              g->v_ptr, g->v_col, g->v_val, x_bf16, ldx, W, ldw,
@@ -347,7 +362,7 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
                                      g->v_col, g->v_val, x_f32, ldx, W, ldw, nchunk, ep, part,
                                      ldw, s));
     } else {
-      EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0};
+      EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0, d};
       ABG_TRY(dispatch_spmm<float>(&g->sched_v, g->sched_v.light, g->sched_v.n_light, g->v_ptr,
                                    g->v_col, g->v_val, zhat, ldz, W, ldw, nchunk, ep, part, ldw,
                                    s));
@@ -364,7 +379,7 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
 int spmm_plain(const int64_t* ptr, const int32_t* col, const float* val, int64_t rows,
                const float* B, int64_t ldb, int n, float* C, int64_t ldc, cudaStream_t s) {
   ABG_CHECK(n >= 1 && n <= kMaxD, "spmm: width out of range");
-  EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0};
+  EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0, n};
   return dispatch_spmm<float>(nullptr, nullptr, rows, ptr, col, val, B, ldb, C, ldc, (n + 3) / 4,
                               ep, nullptr, 0, s);
 }

@@ -305,3 +305,46 @@ def test_invalid_parameters_rejected():
             abg.abg_cluster(h, abg.params(**bad))
         assert e.value.status == abg.ABG_EINVAL
     h.close()
+
+
+def _nan_padded(a: np.ndarray):
+    """Device copy of `a` whose row padding (columns width..ld-1) holds NaN."""
+    t = dev(a)
+    if t.shape[1] > a.shape[1]:
+        t[:, a.shape[1]:] = float("nan")
+    return t
+
+
+def test_row_padding_is_ignored_by_every_step():
+    # widths that are not multiples of 4 leave padding columns in every row; whatever the
+    # caller keeps there (here NaN) must not reach any result
+    g = synth.make_small(21, n_u=300, n_v=400, k=3, d_u=6, deg=5)
+    h = abg.abg_create(g)
+    X = g.x_dense_f64()
+    zh = empty(g.n_u, 6)
+    abg.abg_propagate(h, _nan_padded(X), 6, 0.6, 4, zh)
+    ref_z = tpo.normalize_rows(tpo.propagate(oracle_L(g), X.astype(np.float32).astype(np.float64),
+                                             0.6, 4))
+    got = host(zh, 6)
+    assert np.all(np.isfinite(got)) and np.abs(got - ref_z).max() < 2e-5
+    assert torch.all(zh[:, 6:] == 0)                       # padding written back as 0
+    Zh = ref_z.astype(np.float32).astype(np.float64)
+    R = empty(g.n_u, 12)
+    abg.abg_random_features(_nan_padded(Zh), g.n_u, 6, 4, R)
+    _, _, ref_r, _ = tpo.random_features(Zh, tpo.orthogonal_matrix(4, 6))
+    assert np.abs(host(R, 12) - ref_r).max() <= 2e-4 * np.abs(ref_r).max()
+    Rm = ref_r.astype(np.float32).astype(np.float64)[:, :11]     # width 11: one padding column
+    phi, H = empty(g.n_u, 3), empty(11, 3)
+    abg.abg_seed_factors(_nan_padded(Rm), g.n_u, 11, 3, phi, H, seed=2)
+    assert torch.isfinite(phi[:, :3]).all() and torch.isfinite(H[:, :3]).all()
+    P0, H0, _ = tpo.seed_factors(Rm, 3, 2)
+    assert np.abs(host(phi, 3) - P0).max() <= 1e-3 * np.abs(P0).max()
+    labels = torch.zeros(g.n_u, dtype=torch.int32, device=DEV)
+    abg.abg_nci(_nan_padded(P0), g.n_u, 3, 5, labels)
+    rl, _, rm, _ = tpo.nci(P0.astype(np.float32).astype(np.float64), 5)
+    sure = rm > 1e-4
+    assert np.array_equal(labels.cpu().numpy()[sure], rl[sure])
+    obj = abg.abg_objective(_nan_padded(Rm), g.n_u, 11, labels, 3)
+    ref_o = tpo.objective(Rm, labels.cpu().numpy(), 3)
+    assert obj[0] == pytest.approx(ref_o[0], rel=1e-5)
+    h.close()

@@ -1,0 +1,92 @@
+"""The continuous-batching request loop on the GPU: every served result equals the same request
+solved alone (bitwise), requests of two attribute layouts mix in one stream, polls time out
+while work is pending, and admission keeps the footprint within the budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2405_11922_gb300 as abg  # noqa: E402
+
+
+def _requests():
+    reqs = []
+    for i in range(14):
+        n_u = [80, 500, 2000, 9000, 150, 30000, 700][i % 7]
+        kind = "csr_f32" if i % 2 else "dense_bf16"
+        d_u = 40 if kind == "csr_f32" else 16
+        g = synth.make_small(500 + i, n_u=n_u, n_v=int(1.5 * n_u), k=3 + i % 5, d_u=d_u, deg=6,
+                             x_kind=kind, signal=3.0)
+        d = 8 if kind == "csr_f32" else 16
+        p = abg.params(k=3 + i % 5, alpha=0.6, gamma=4, d=d, t_f=4, t_g=8, seed=1000 + i)
+        reqs.append((g, p))
+    return reqs
+
+
+def _alone(g, p):
+    h = abg.abg_create(g)
+    lab, res = abg.abg_cluster(h, p)
+    h.close()
+    return lab, res
+
+
+def test_served_results_equal_alone():
+    reqs = _requests()
+    sv = abg.Server(workers=3, max_batch_graphs=6)
+    rids = []
+    for g, p in reqs:                 # arrivals spread over time so batches form as work runs
+        rids.append(sv.submit(g, p))
+        time.sleep(0.002)
+    for (g, p), rid in zip(reqs, rids):
+        st, lab, res = sv.poll(rid, 60_000_000)
+        assert st == abg.ABG_OK
+        lab1, res1 = _alone(g, p)
+        assert np.array_equal(lab, lab1)
+        assert res.objective == res1.objective
+    s = sv.stats()
+    assert s["completed"] == len(reqs) and s["inflight_bytes"] == 0
+    assert s["batches"] < len(reqs)   # requests were batched together
+    sv.close()
+
+
+def test_poll_timeout_and_pending():
+    g = synth.make_config3(scale=0.05, k=10)    # a request that takes a while
+    sv = abg.Server(workers=1)
+    rid = sv.submit(g, abg.params(k=10, alpha=0.9, gamma=10, d=128))
+    st, _, _ = sv.poll(rid, 0)
+    assert st in (abg.ABG_PENDING, abg.ABG_OK)
+    if st == abg.ABG_PENDING:
+        st2, _, _ = sv.poll(rid, 1)               # 1 microsecond
+        assert st2 in (abg.ABG_ETIMEDOUT, abg.ABG_OK)
+        if st2 == abg.ABG_ETIMEDOUT:
+            st3, lab, _ = sv.poll(rid, -1)
+            assert st3 == abg.ABG_OK and lab.shape == (g.n_u,)
+    sv.close()
+
+
+def test_budget_serialises_requests():
+    # a budget for about two requests: everything completes, the accounting returns to zero
+    reqs = _requests()[:6]
+    est = []
+    for g, p in reqs:
+        h = abg.abg_create(g)
+        est.append(h.footprint() + abg.abg_solve_footprint(h, p))
+        h.close()
+    sv = abg.Server(workers=3, hbm_budget_bytes=2 * max(est) + (256 << 20), max_batch_graphs=1)
+    rids = [sv.submit(g, p) for g, p in reqs]
+    assert all(r > 0 for r in rids)
+    for rid in rids:
+        st, _, _ = sv.poll(rid, 60_000_000)
+        assert st == abg.ABG_OK
+    s = sv.stats()
+    assert s["completed"] == 6 and s["inflight_bytes"] == 0 and s["max_batch"] == 1
+    sv.close()
