@@ -301,6 +301,180 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched workload: 512 independent graphs, one at a time vs one batch
+# ---------------------------------------------------------------------------
+
+def _gen_config4(g):
+    import synth
+    return synth.make_config4_graph(g)
+
+
+def _gen_config5(r):
+    import synth
+    return synth.make_config5_request(r)
+
+
+def _pool_map(fn, items, workers=None):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers or min(16, os.cpu_count() or 4)) as pool:
+        return pool.map(fn, items, chunksize=max(1, len(items) // 64))
+
+
+def _params4(abg, g, i):
+    return abg.params(k=g.k, alpha=0.6, gamma=6, d=32, t_f=5, t_g=20, seed=i)
+
+
+def run_batched(args):
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    n = args.graphs
+    graphs = _pool_map(_gen_config4, list(range(n)))
+    params = [_params4(abg, g, i) for i, g in enumerate(graphs)]
+    rows = sum(g.n_u for g in graphs)
+    stream = torch.cuda.current_stream()
+    # ---- plain: one graph at a time, graphs resident ----
+    handles = [abg.abg_create(g, stream=stream) for g in graphs]
+    for h, p in list(zip(handles, params))[:args.warmup]:
+        abg.abg_cluster(h, p, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_labels = [abg.abg_cluster(h, p, stream=stream)[0] for h, p in zip(handles, params)]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    for h in handles:
+        h.close()
+    # ---- batched: all graphs in one batch, resident ----
+    batch = abg.abg_batch_create(graphs, stream=stream)
+    for _ in range(max(1, args.warmup)):
+        abg.abg_batch_cluster(batch, params, stream=stream)
+    torch.cuda.synchronize()
+    l0 = abg.abg_launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        blab, bres = abg.abg_batch_cluster(batch, params, stream=stream)
+    torch.cuda.synchronize()
+    batch_s = (time.perf_counter() - t0) / args.steps
+    launches = (abg.abg_launch_count() - l0) // args.steps
+    batch.close()
+    # ---- end to end: uploads included ----
+    t0 = time.perf_counter()
+    for g, p in zip(graphs, params):
+        h = abg.abg_create(g, stream=stream)
+        abg.abg_cluster(h, p, stream=stream)
+        h.close()
+    plain_e2e = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = abg.abg_batch_create(graphs, stream=stream)
+    abg.abg_batch_cluster(b, params, stream=stream)
+    b.close()
+    batch_e2e = time.perf_counter() - t0
+    same = 0
+    off = 0
+    for g, lab in zip(graphs, plain_labels):
+        same += int(np.array_equal(blab[off:off + g.n_u], lab))
+        off += g.n_u
+    line = {"metric": "batched TPO solves/s (many small ABGs per launch) vs one graph at a time",
+            "value": n / batch_s, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * batch_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n} planted ABGs, |U| log-uniform [500, 50000], "
+                                   "|V| = 1.5|U|, 10 edge draws per u, k ~ U{3..30}, binary "
+                                   "attributes d_u=300 at 3% reduced to d=32, alpha=0.6, "
+                                   "gamma=6, T_f=5, T_g=20", "total_u": int(rows)},
+            "plain_solves_per_s": n / plain_s, "speedup_vs_plain": plain_s / batch_s,
+            "e2e": {"batched_solves_per_s": n / batch_e2e, "plain_solves_per_s": n / plain_e2e},
+            "identical_to_plain": f"{same}/{n}", "gpu_launches_per_batch": int(launches)}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# served workload: Poisson arrivals, continuous batching vs plain sequential
+# ---------------------------------------------------------------------------
+
+def run_serve(args):
+    import threading
+
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    import synth
+    pool = _pool_map(_gen_config5, list(range(args.pool)))
+    arrivals = synth.config5_arrivals(args.requests, rate=args.rate)
+    reqs = []
+    for r in range(args.requests):
+        g = pool[r % len(pool)]
+        p = abg.params(k=g.params["k"], alpha=0.6, gamma=6, d=g.params["d"], t_f=5, t_g=20,
+                       seed=r)
+        reqs.append((g, p))
+    stream = torch.cuda.current_stream()
+    # warm-up of both paths on a few requests
+    for g, p in reqs[:3]:
+        h = abg.abg_create(g, stream=stream)
+        abg.abg_cluster(h, p, stream=stream)
+        h.close()
+    # ---- served ----
+    sv = abg.Server(workers=args.workers, max_batch_graphs=args.max_batch,
+                    hbm_budget_bytes=int(args.budget_gb * (1 << 30)))
+    rids = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, (g, p) in enumerate(reqs):
+            wait = t_start + arrivals[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            rids[i] = sv.submit(g, p)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    served_lat, served_labels = [], []
+    for i in range(len(reqs)):
+        while rids[i] is None:
+            time.sleep(0.0005)
+        st, lab, _ = sv.poll(rids[i], -1)
+        assert st == abg.ABG_OK, st
+        served_lat.append(sv.stats()["latency_us_last"] / 1e6)
+        served_labels.append(lab)
+    th.join()
+    served_total = time.perf_counter() - t_start
+    stats = sv.stats()
+    sv.close()
+    # ---- plain sequential (same arrival process, one request at a time) ----
+    plain_lat, same = [], 0
+    t_start = time.perf_counter()
+    for i, (g, p) in enumerate(reqs):
+        wait = t_start + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        h = abg.abg_create(g, stream=stream)
+        lab, _ = abg.abg_cluster(h, p, stream=stream)
+        h.close()
+        plain_lat.append(time.perf_counter() - (t_start + arrivals[i]))
+        same += int(np.array_equal(lab, served_labels[i]))
+    plain_total = time.perf_counter() - t_start
+    q = lambda v, x: float(np.percentile(v, x)) * 1e3
+    line = {"metric": "served TPO solves/s and p50/p99 latency vs plain sequential FP32",
+            "value": len(reqs) / served_total, "unit": "solves/s", "n_gpus": 1,
+            "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * served_total / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, "
+                                   f"graphs drawn from a pool of {len(pool)}: |U| log-uniform "
+                                   "[1000, 1e6], |V| = 2.5|U|, 25 draws per u, k ~ U{5..100}, "
+                                   "half dense d=128 BF16, half sparse d_u=500 reduced to 64",
+                       "workers": args.workers, "max_batch": args.max_batch},
+            "served": {"solves_per_s": len(reqs) / served_total, "p50_ms": q(served_lat, 50),
+                       "p99_ms": q(served_lat, 99), "batches": stats["batches"],
+                       "max_batch": stats["max_batch"]},
+            "plain": {"solves_per_s": len(reqs) / plain_total, "p50_ms": q(plain_lat, 50),
+                      "p99_ms": q(plain_lat, 99)},
+            "identical_to_plain": f"{same}/{len(reqs)}"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,12 +483,25 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["large", "batched", "serve"], default="large")
+    ap.add_argument("--graphs", type=int, default=512, help="batched workload: number of graphs")
+    ap.add_argument("--requests", type=int, default=200, help="served workload: requests")
+    ap.add_argument("--pool", type=int, default=32, help="served workload: distinct graphs")
+    ap.add_argument("--rate", type=float, default=200.0, help="served workload: arrivals/s")
+    ap.add_argument("--workers", type=int, default=3)
+    ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "large":
+        import torch
+        torch.cuda.set_device(local_rank)
+        (run_batched if args.workload == "batched" else run_serve)(args)
         return
     if world > 1:
         import torch
