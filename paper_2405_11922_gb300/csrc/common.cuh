@@ -51,6 +51,8 @@ void note_launch();
 // stream-ordered device memory from a private pool per device
 // ---------------------------------------------------------------------------
 int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+// Raises (never lowers) func's dynamic shared-memory limit on the current device.
+int raise_smem_limit(const void* func, size_t bytes);
 void dev_free(void* p, cudaStream_t s);
 
 // RAII holder used inside one call: everything is released (stream-ordered)

@@ -4,7 +4,7 @@
 //     R Q, R H, Phi C, Q_b U (Algorithm 2 and its randomized SVD), Zhat Q^T
 //     (Eq. 13) and Phi T (Eq. 21), each with a fused epilogue.
 //   * gemm_tn: C_s = A^T B reduced over the rows of segment s (R^T Phi,
-//     Phi^T Phi, Phi^T (R H), Gram matrices): FP32 products per fixed
+//     Phi^T Phi, Gram matrices): FP32 products per fixed
 //     2048-row chunk, chunk partials summed in FP64 in a fixed order.
 //   * random features (Eqs. 13-14), the H rule (Eq. 16), NCI generation
 //     (Algorithm 3, Eqs. 21-23) and the objective (Eq. 8).
@@ -584,6 +584,34 @@ int nmf_update_h(int nseg, int m, const int* segk, int kmax, float* H, int64_t l
   return ABG_OK;
 }
 
+// C_s[p][q] = sum_{j < m} A_s[j][p] H_s[j][q] for p, q < k_s (A FP64, H FP32, C FP64)
+__global__ void k_small_atb(int m, const int* __restrict__ segk, int kmax,
+                            const double* __restrict__ A, int64_t lda, int64_t aseg,
+                            const float* __restrict__ H, int64_t ldh, int64_t hseg,
+                            double* __restrict__ C, int64_t ldc, int64_t cseg) {
+  const int sg = blockIdx.y;
+  const int k = segk[sg];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kmax * kmax) return;
+  const int p = idx / kmax, q = idx % kmax;
+  if (p >= k || q >= k) return;
+  const double* As = A + sg * aseg;
+  const float* Hs = H + sg * hseg;
+  double acc = 0.0;
+  for (int j = 0; j < m; ++j) acc += As[(int64_t)j * lda + p] * (double)Hs[(int64_t)j * ldh + q];
+  C[sg * cseg + (int64_t)p * ldc + q] = acc;
+}
+
+int small_atb(int nseg, int m, const int* segk, int kmax, const double* A, int64_t lda,
+              int64_t aseg, const float* H, int64_t ldh, int64_t hseg, double* C, int64_t ldc,
+              int64_t cseg, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div((int64_t)kmax * kmax, 128), (unsigned)nseg);
+  k_small_atb<<<grid, 128, 0, s>>>(m, segk, kmax, A, lda, aseg, H, ldh, hseg, C, ldc, cseg);
+  note_launch();
+  ABG_LAUNCH_CHECK();
+  return ABG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Per-chunk cluster sums S[l][m] = sum_{i in chunk, label i = l} X[i, m] and counts (one
 // thread per column, rows in order: deterministic). Labels outside [0, kmax) are skipped.
@@ -644,9 +672,7 @@ static int cluster_sums(const RowSpace& rs, const float* X, int w, int64_t ldx,
   float* part;
   ABG_TRY(scr.get(&part, (size_t)std::max<int64_t>(1, rs.n_chunks) * width));
   const size_t smem = sizeof(float) * ((size_t)kmax * wtile + kmax);
-  if (smem > 48 * 1024)
-    ABG_CUDA(cudaFuncSetAttribute(k_cluster_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  ABG_TRY(raise_smem_limit((const void*)k_cluster_sums, smem));
   const int threads = (int)round_up(wtile, 32);
   for (int col0 = 0; col0 < w; col0 += wtile) {
     if (!rs.n_chunks) break;

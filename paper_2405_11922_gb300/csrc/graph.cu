@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -53,6 +54,24 @@ static int pool_for_current(cudaMemPool_t* out) {
     ABG_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr));
   }
   *out = g_pool[dev];
+  return ABG_OK;
+}
+
+// The dynamic shared-memory limit of a kernel is one setting per context, so
+// concurrent callers only ever raise it: a launch that needs b bytes finds a
+// limit >= b however other threads interleave.
+static std::mutex g_smem_mu;
+static std::map<std::pair<const void*, int>, size_t> g_smem_limit;
+
+int raise_smem_limit(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return ABG_OK;
+  int dev = 0;
+  ABG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& cur = g_smem_limit[{func, dev}];
+  if (cur >= bytes) return ABG_OK;
+  ABG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
   return ABG_OK;
 }
 

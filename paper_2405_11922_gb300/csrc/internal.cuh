@@ -145,6 +145,10 @@ int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, c
 int nmf_update_h(int nseg, int m, const int* segk, int kmax, float* H, int64_t ldh, int64_t hseg,
                  const double* A, int64_t lda, int64_t aseg, const double* G, int64_t ldg,
                  int64_t gseg, cudaStream_t s);
+// C_s (k_s x k_s, FP64) = A_s^T H_s with A_s (m x k_s, FP64) and H_s (m x k_s, FP32).
+int small_atb(int nseg, int m, const int* segk, int kmax, const double* A, int64_t lda,
+              int64_t aseg, const float* H, int64_t ldh, int64_t hseg, double* C, int64_t ldc,
+              int64_t cseg, cudaStream_t s);
 // Algorithm 3 (all t_g passes) per segment. counters (device, 3*nseg ints): last-pass label
 // changes, minimum margin (float bits), empty clusters.
 int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ldphi, int t_g,

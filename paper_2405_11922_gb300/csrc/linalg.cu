@@ -196,9 +196,7 @@ static int chol_inv(int nseg, const int* segl, int lmax, const double* G, int64_
                     int* breakdowns, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * (size_t)lmax * lmax;
   const int in_smem = smem <= 200 * 1024;
-  if (in_smem)
-    ABG_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  if (in_smem) ABG_TRY(raise_smem_limit((const void*)k_chol_inv, smem));
   k_chol_inv<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(segl, lmax, G, ldg, gseg, R, Ri, rseg,
                                                               ri32, ldr32, r32seg, breakdowns,
                                                               in_smem);
@@ -344,8 +342,10 @@ int orthogonal_matrices(int nseg, const uint64_t* seeds, int d, double* q, cudaS
 // CholeskyQR2 of tall FP32 blocks per segment: two passes of Gram (FP64, via
 // gemm_tn) -> Cholesky -> Y R^-1 (FP32 GEMM).
 // ---------------------------------------------------------------------------
-int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy, float* tmp,
-            int64_t ldt, int* breakdowns, cudaStream_t s) {
+// One CholeskyQR pass per segment: dst = src R^-1 with R^T R = src^T src (FP64 Gram and
+// Cholesky, FP32 product).
+static int cholqr_pass(const RowSpace& rs, const int* segl, int lmax, const float* src,
+                       int64_t lds, float* dst, int64_t ldd, int* breakdowns, cudaStream_t s) {
   Scratch scr(s);
   const int64_t ll = round_up(lmax, 4);
   const int64_t l2 = (int64_t)lmax * lmax;
@@ -356,36 +356,34 @@ int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy
   ABG_TRY(scr.get(&R, (size_t)nseg * l2));
   ABG_TRY(scr.get(&Ri, (size_t)nseg * l2));
   ABG_TRY(scr.get(&ri32, (size_t)nseg * lmax * ll));
-  for (int pass = 0; pass < 2; ++pass) {
-    float* src = pass == 0 ? Y : tmp;
-    const int64_t lds = pass == 0 ? ldy : ldt;
-    float* dst = pass == 0 ? tmp : Y;
-    const int64_t ldd = pass == 0 ? ldt : ldy;
-    TN g;
-    g.A = g.B = src;
-    g.lda = g.ldb = lds;
-    g.K = g.N = lmax;
-    g.segK = g.segN = segl;
-    g.C = Gram;
-    g.ldc = lmax;
-    g.c_seg = l2;
-    ABG_TRY(gemm_tn(rs, g, s));
-    // R_s / Ri_s use the segment's own l_s as row stride inside their l2 slabs
-    ABG_TRY(chol_inv(nseg, segl, lmax, Gram, lmax, l2, R, Ri, l2, ri32, ll, lmax * ll, breakdowns,
-                     s));
-    NN a;
-    a.A = src;
-    a.lda = lds;
-    a.B = ri32;
-    a.ldb = ll;
-    a.b_seg = lmax * ll;
-    a.C = dst;
-    a.ldc = ldd;
-    a.N = a.K = lmax;
-    a.segN = a.segK = segl;
-    ABG_TRY(gemm_nn(rs, a, s));
-  }
-  return ABG_OK;
+  TN g;
+  g.A = g.B = src;
+  g.lda = g.ldb = lds;
+  g.K = g.N = lmax;
+  g.segK = g.segN = segl;
+  g.C = Gram;
+  g.ldc = lmax;
+  g.c_seg = l2;
+  ABG_TRY(gemm_tn(rs, g, s));
+  // R_s / Ri_s use the segment's own l_s as row stride inside their l2 slabs
+  ABG_TRY(chol_inv(nseg, segl, lmax, Gram, lmax, l2, R, Ri, l2, ri32, ll, lmax * ll, breakdowns, s));
+  NN a;
+  a.A = src;
+  a.lda = lds;
+  a.B = ri32;
+  a.ldb = ll;
+  a.b_seg = lmax * ll;
+  a.C = dst;
+  a.ldc = ldd;
+  a.N = a.K = lmax;
+  a.segN = a.segK = segl;
+  return gemm_nn(rs, a, s);
+}
+
+int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy, float* tmp,
+            int64_t ldt, int* breakdowns, cudaStream_t s) {
+  ABG_TRY(cholqr_pass(rs, segl, lmax, Y, ldy, tmp, ldt, breakdowns, s));
+  return cholqr_pass(rs, segl, lmax, tmp, ldt, Y, ldy, breakdowns, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,8 +522,7 @@ static int jacobi_eig(int nseg, const int* segl, int lmax, double* A, double* ev
   const int a_smem = base + mat <= limit;
   const int v_smem = a_smem && base + 2 * mat <= limit;
   const size_t smem = base + (a_smem ? mat : 0) + (v_smem ? mat : 0);
-  if (smem > 48 * 1024)
-    ABG_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ABG_TRY(raise_smem_limit((const void*)k_jacobi, smem));
   k_jacobi<<<(unsigned)nseg, threads, smem, s>>>(segl, lmax, A, V, evals, evecs, 40, a_smem, v_smem);
   note_launch();
   ABG_LAUNCH_CHECK();
@@ -653,17 +650,33 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   ABG_TRY(scr.get(&Bm, (size_t)nseg * lmax * kk));
   RowSpace small;  // m rows per segment (the Omega / A^T Q side)
   ABG_TRY(rowspace_uniform(&small, nseg, m, scr, s));
-  // range finder
+  // range finder: the intermediate bases only need to stay well conditioned (one
+  // CholeskyQR pass each); the final tall basis gets CholeskyQR2
   ABG_TRY(gaussian_f32(nseg, ss.seed, stream_id, m, lmax, ss.l, Om, ll, (int64_t)m * ll, s));
-  ABG_TRY(apply_a(in, ss.l, lmax, Om, ll, Y, ll, s));
-  ABG_TRY(cholqr2(rs, ss.l, lmax, Y, ll, T1, ll, breakdowns, s));
-  for (int it = 0; it < power_iters; ++it) {
-    ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
-    ABG_TRY(convert_f64_to_f32(Bt, (int64_t)nseg * m, lmax, lmax, Yt, ll, s));
-    ABG_TRY(cholqr2(small, ss.l, lmax, Yt, ll, T2, ll, breakdowns, s));
-    ABG_TRY(apply_a(in, ss.l, lmax, Yt, ll, Y, ll, s));
-    ABG_TRY(cholqr2(rs, ss.l, lmax, Y, ll, T1, ll, breakdowns, s));
+  float* Ya = Y;
+  float* Yb = T1;
+  ABG_TRY(apply_a(in, ss.l, lmax, Om, ll, Ya, ll, s));
+  float* cur = Ya;
+  if (power_iters == 0) {
+    ABG_TRY(cholqr2(rs, ss.l, lmax, Ya, ll, Yb, ll, breakdowns, s));
+  } else {
+    ABG_TRY(cholqr_pass(rs, ss.l, lmax, Ya, ll, Yb, ll, breakdowns, s));
+    cur = Yb;
   }
+  for (int it = 0; it < power_iters; ++it) {
+    ABG_TRY(apply_at(in, ss.l, lmax, cur, ll, Bt, T2, ll, s));
+    ABG_TRY(convert_f64_to_f32(Bt, (int64_t)nseg * m, lmax, lmax, Yt, ll, s));
+    ABG_TRY(cholqr_pass(small, ss.l, lmax, Yt, ll, T2, ll, breakdowns, s));
+    float* nxt = cur == Ya ? Yb : Ya;
+    ABG_TRY(apply_a(in, ss.l, lmax, T2, ll, nxt, ll, s));
+    if (it == power_iters - 1) {
+      ABG_TRY(cholqr2(rs, ss.l, lmax, nxt, ll, cur, ll, breakdowns, s));
+      cur = nxt;
+    } else {
+      ABG_TRY(cholqr_pass(rs, ss.l, lmax, nxt, ll, cur, ll, breakdowns, s));
+    }
+  }
+  Y = cur;
   // B^T = A^T Q (m x l), B B^T = Bt^T Bt (l x l), eigenpairs
   ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
   {

@@ -164,17 +164,10 @@ int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int 
     pr.K = m;
     pr.segN = ss.k;
     ABG_TRY(gemm_nn(rs, pr, s));
-    TN tc;
-    tc.A = cur;
-    tc.lda = ldphi;
-    tc.B = P;
-    tc.ldb = ldphi;
-    tc.K = tc.N = kmax;
-    tc.segK = tc.segN = ss.k;
-    tc.C = C;
-    tc.ldc = kmax;
-    tc.c_seg = (int64_t)kmax * kmax;
-    ABG_TRY(gemm_tn(rs, tc, s));
+    // Phi^T (R H) = (R^T Phi)^T H: the tall reduction R^T Phi of the H rule (same Phi) is
+    // reused, so only a k x 2d x k product remains
+    ABG_TRY(small_atb(nseg, m, ss.k, kmax, A, kmax, (int64_t)m * kmax, H, ldh, hseg, C, kmax,
+                      (int64_t)kmax * kmax, s));
     ABG_TRY(convert_f64_to_f32(C, (int64_t)nseg * kmax, kmax, kmax, C32, kk, s));
     NN pu;
     pu.A = cur;

@@ -15,6 +15,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -32,6 +33,7 @@ struct Job {
   int status = ABG_PENDING;
   std::vector<int32_t> labels;
   abg_result result{};
+  std::string error;  // message of a failed batch, handed to the poller
   clock_t_::time_point t_submit, t_done;
 };
 
@@ -145,6 +147,7 @@ void worker_main(abg_server* sv, int wid) {
     int st = abg_batch_create(descs.data(), (int32_t)descs.size(), sv->opts.device, stream, &g);
     if (st == ABG_OK)
       st = abg_batch_cluster(g, params.data(), stream, labels.data(), res.data());
+    const std::string err = st == ABG_OK ? std::string() : std::string(abg_last_error());
     if (g) abg_destroy(g);
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -155,6 +158,8 @@ void worker_main(abg_server* sv, int wid) {
         if (st == ABG_OK) {
           j->labels.assign(labels.begin() + off, labels.begin() + off + j->desc.n_u);
           j->result = res[i];
+        } else {
+          j->error = err;
         }
         off += j->desc.n_u;
         j->status = st;
@@ -275,6 +280,7 @@ ABG_API int abg_poll(abg_server* sv, uint64_t req_id, int64_t timeout_us, int32_
   }
   if (j->status == ABG_PENDING) return timeout_us == 0 ? ABG_PENDING : ABG_ETIMEDOUT;
   const int st = j->status;
+  const std::string err = j->error;
   if (st == ABG_OK) {
     if (labels) memcpy(labels, j->labels.data(), sizeof(int32_t) * j->labels.size());
     if (res) *res = j->result;
@@ -283,7 +289,8 @@ ABG_API int abg_poll(abg_server* sv, uint64_t req_id, int64_t timeout_us, int32_
       std::chrono::duration_cast<std::chrono::microseconds>(j->t_done - j->t_submit).count();
   sv->jobs.erase(it);
   delete j;
-  if (st != ABG_OK && st != ABG_ENOTADMITTED) set_error("request failed: %s", abg_strerror(st));
+  if (st != ABG_OK && st != ABG_ENOTADMITTED)
+    set_error("request failed: %s (%s)", abg_strerror(st), err.c_str());
   return st;
 }
 

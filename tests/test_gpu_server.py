@@ -48,7 +48,7 @@ def test_served_results_equal_alone():
         time.sleep(0.002)
     for (g, p), rid in zip(reqs, rids):
         st, lab, res = sv.poll(rid, 60_000_000)
-        assert st == abg.ABG_OK
+        assert st == abg.ABG_OK, abg.lib().abg_last_error().decode()
         lab1, res1 = _alone(g, p)
         assert np.array_equal(lab, lab1)
         assert res.objective == res1.objective
@@ -90,3 +90,36 @@ def test_budget_serialises_requests():
     s = sv.stats()
     assert s["completed"] == 6 and s["inflight_bytes"] == 0 and s["max_batch"] == 1
     sv.close()
+
+
+def test_concurrent_solves_of_different_widths():
+    # host threads solving graphs whose block widths (and so the shared-memory sizes of the
+    # one-CTA Cholesky / Jacobi kernels) differ, at the same time: every result equals the
+    # same solve run alone
+    cases = []
+    for i, (d_u, d, k) in enumerate([(16, 16, 3), (40, 8, 5), (64, 64, 20), (24, 24, 40)]):
+        g = synth.make_small(900 + i, n_u=1500, n_v=2000, k=k, d_u=d_u, deg=6,
+                             x_kind="dense_bf16", signal=3.0)
+        p = abg.params(k=k, alpha=0.6, gamma=3, d=d, t_f=3, t_g=5, seed=77 + i)
+        cases.append((g, p))
+    want = [_alone(g, p) for g, p in cases]
+    handles = [abg.abg_create(g) for g, _ in cases]
+    errors = []
+
+    def run(i):
+        try:
+            for _ in range(6):
+                lab, res = abg.abg_cluster(handles[i], cases[i][1])
+                if not (np.array_equal(lab, want[i][0]) and res.objective == want[i][1].objective):
+                    errors.append(f"case {i}: result differs from the solve run alone")
+        except Exception as e:          # noqa: BLE001
+            errors.append(f"case {i}: {e}")
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for h in handles:
+        h.close()
+    assert not errors, errors
