@@ -35,6 +35,16 @@ METRIC = ("TPO iterations/s and SpMM HBM GB/s at |U|=2M; solves/s + p99 latency 
 WORKLOAD = dict(workload="planted ABG |U|=2M |V|=5M 50M edge draws, Chung-Lu 2.2, 60/40 mixing, "
                          "dense BF16 attributes d=128, k=100, alpha=0.9, gamma=10, T_f=5, T_g=20",
                 n_u=2_000_000, n_v=5_000_000, d=128, k=100)
+def workload_of(g, scale: float) -> dict:
+    """The config label; a scaled-down run names its own sizes."""
+    if scale == 1.0:
+        return dict(WORKLOAD)
+    return dict(workload=f"planted ABG |U|={g.n_u} |V|={g.n_v} (config scaled by {scale}), "
+                         "Chung-Lu 2.2, 60/40 mixing, dense BF16 attributes d=128, k=100, "
+                         "alpha=0.9, gamma=10, T_f=5, T_g=20",
+                n_u=int(g.n_u), n_v=int(g.n_v), d=128, k=100, scale=scale)
+
+
 PARAMS = dict(k=100, alpha=0.9, gamma=10, d=128, t_f=5, t_g=20, seed=0)
 ORACLE_SCALES = (0.01, 0.02)   # oracle sample sizes (fraction of the full workload)
 
@@ -278,7 +288,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(WORKLOAD, nnz=int(g.nnz), parallelism=f"{world} independent solves "
+        "config": dict(workload_of(g, args.scale), nnz=int(g.nnz),
+                       parallelism=f"{world} independent solves "
                        "(one graph per rank)" if world > 1 else "single GPU",
                        l2="inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"),
         "tpo_prop_iters_per_s": PARAMS["gamma"] / (prop_ms / 1e3),
@@ -287,7 +298,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                               "objective"], phase_ms)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "propagation SpMMs (k_spmm_rows/chunks/reduce, gamma rounds)",
+                     "kernel": "propagation SpMMs (k_spmm_stream/chunks/reduce, gamma rounds)",
                      "peak_kind": peak_kind},
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},

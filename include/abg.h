@@ -220,7 +220,9 @@ ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversam
  * Z <- (1-a) X + a L (L^T Z), gamma times), then Eq. 2: zhat[n_u][ldz] holds
  * the row-normalised Z_U (a zero row stays zero). x = NULL uses the graph's
  * own dense attributes (d must equal d_u); otherwise x[n_u][ldx] (device,
- * float) is the attribute matrix of width d (e.g. abg_reduce_attributes). */
+ * float) is the attribute matrix of width d (e.g. abg_reduce_attributes).
+ * Returns once the work on `stream` has finished (it then checks the gather
+ * pipeline's bounded waits: ABG_EDEVICE if one ran out). */
 ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32_t d,
                           double alpha, int32_t gamma, float* zhat, int64_t ldz, void* stream);
 

@@ -94,7 +94,7 @@ void dev_free(void* p, cudaStream_t s) {
 }
 
 int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s) {
-  if (g->n_blocks >= 32) {
+  if (g->n_blocks >= 64) {
     set_error("internal: too many graph blocks");
     return ABG_ENOMEM;
   }
@@ -192,51 +192,63 @@ static void build_csc(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t* u_pt
     }
 }
 
-// Row schedule of one SpMM direction: light rows by decreasing degree (coarse
-// log2 buckets, stable), heavy rows cut into kHeavyChunk-edge chunks.
+// Row schedule of one SpMM direction: light rows grouped into tasks of at most
+// kTaskRows consecutive rows and about kTaskEdges edges (a task never spans a
+// heavy row), heavy rows cut into kHeavyChunk-edge chunks.
 static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_graph::Schedule& sc,
                           cudaStream_t s) {
-  std::vector<int32_t> light;
+  std::vector<int32_t> tasks;  // (first row, one past the last row) of each light task
   std::vector<int64_t> cb;
   std::vector<int32_t> cslot;
   std::vector<int32_t> hrow;
   std::vector<int64_t> hc0;
-  light.reserve(rows);
-  std::vector<int64_t> bucket_count(64, 0);
-  auto bucket = [](int64_t deg) { return deg <= 0 ? 0 : 64 - __builtin_clzll((uint64_t)deg); };
+  int64_t t_r0 = -1, t_edges = 0;
+  auto close_task = [&](int64_t r_end) {
+    if (t_r0 >= 0) {
+      tasks.push_back((int32_t)t_r0);
+      tasks.push_back((int32_t)r_end);
+    }
+    t_r0 = -1;
+    t_edges = 0;
+  };
   for (int64_t r = 0; r < rows; ++r) {
-    int64_t deg = ptr[r + 1] - ptr[r];
+    const int64_t deg = ptr[r + 1] - ptr[r];
     if (deg > kHeavyRow) {
+      close_task(r);
       hc0.push_back((int64_t)cb.size());
-      int32_t slot = (int32_t)hrow.size();
+      const int32_t slot = (int32_t)hrow.size();
       hrow.push_back((int32_t)r);
       for (int64_t b = ptr[r]; b < ptr[r + 1]; b += kHeavyChunk) {
         cb.push_back(b);
         cslot.push_back(slot);
       }
-    } else {
-      bucket_count[bucket(deg)]++;
+      continue;
     }
+    if (t_r0 >= 0 && (r - t_r0 >= kTaskRows || t_edges + deg > kTaskEdges)) close_task(r);
+    if (t_r0 < 0) t_r0 = r;
+    t_edges += deg;
   }
+  close_task(rows);
   hc0.push_back((int64_t)cb.size());
-  // descending buckets
-  std::vector<int64_t> start(64, 0);
-  int64_t acc = 0;
-  for (int bk = 63; bk >= 0; --bk) {
-    start[bk] = acc;
-    acc += bucket_count[bk];
+  // the same tasks split by whether they hold edges (the TMA-gather kernel takes those that do)
+  std::vector<int32_t> et, zt;
+  for (size_t i = 0; i < tasks.size(); i += 2) {
+    auto& dst = ptr[tasks[i + 1]] > ptr[tasks[i]] ? et : zt;
+    dst.push_back(tasks[i]);
+    dst.push_back(tasks[i + 1]);
   }
-  light.resize(acc);
-  for (int64_t r = 0; r < rows; ++r) {
-    int64_t deg = ptr[r + 1] - ptr[r];
-    if (deg <= kHeavyRow) light[start[bucket(deg)]++] = (int32_t)r;
-  }
-  sc.n_light = (int64_t)light.size();
+  sc.n_tasks = (int64_t)tasks.size() / 2;
+  sc.n_etasks = (int64_t)et.size() / 2;
+  sc.n_ztasks = (int64_t)zt.size() / 2;
   sc.n_chunks = (int64_t)cb.size();
   sc.n_heavy = (int64_t)hrow.size();
   void* p;
-  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * std::max<int64_t>(1, sc.n_light), s));
-  sc.light = (int32_t*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * 2 * std::max<int64_t>(1, sc.n_tasks), s));
+  sc.tasks = (int2*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * 2 * std::max<int64_t>(1, sc.n_etasks), s));
+  sc.etasks = (int2*)p;
+  ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * 2 * std::max<int64_t>(1, sc.n_ztasks), s));
+  sc.ztasks = (int2*)p;
   ABG_TRY(graph_alloc(g, &p, sizeof(int64_t) * std::max<int64_t>(1, sc.n_chunks), s));
   sc.chunk_begin = (int64_t*)p;
   ABG_TRY(graph_alloc(g, &p, sizeof(int32_t) * std::max<int64_t>(1, sc.n_chunks), s));
@@ -245,8 +257,14 @@ static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_gr
   sc.heavy_row = (int32_t*)p;
   ABG_TRY(graph_alloc(g, &p, sizeof(int64_t) * (sc.n_heavy + 1), s));
   sc.heavy_chunk0 = (int64_t*)p;
-  if (sc.n_light)
-    ABG_CUDA(cudaMemcpyAsync(sc.light, light.data(), sizeof(int32_t) * sc.n_light,
+  if (sc.n_tasks)
+    ABG_CUDA(cudaMemcpyAsync(sc.tasks, tasks.data(), sizeof(int32_t) * 2 * sc.n_tasks,
+                             cudaMemcpyHostToDevice, s));
+  if (sc.n_etasks)
+    ABG_CUDA(cudaMemcpyAsync(sc.etasks, et.data(), sizeof(int32_t) * 2 * sc.n_etasks,
+                             cudaMemcpyHostToDevice, s));
+  if (sc.n_ztasks)
+    ABG_CUDA(cudaMemcpyAsync(sc.ztasks, zt.data(), sizeof(int32_t) * 2 * sc.n_ztasks,
                              cudaMemcpyHostToDevice, s));
   if (sc.n_chunks) {
     ABG_CUDA(cudaMemcpyAsync(sc.chunk_begin, cb.data(), sizeof(int64_t) * sc.n_chunks,
@@ -446,6 +464,12 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
   }
   ABG_TRY(build_schedule(g, d->u_ptr, d->n_u, g->sched_u, s));
   ABG_TRY(build_schedule(g, v_ptr, d->n_v, g->sched_v, s));
+  {
+    void* p;
+    ABG_TRY(graph_alloc(g, &p, sizeof(int), s));
+    g->wait_err = (int*)p;
+    ABG_CUDA(cudaMemsetAsync(g->wait_err, 0, sizeof(int), s));
+  }
   ABG_CUDA(cudaStreamSynchronize(s));
   return ABG_OK;
 }

@@ -38,11 +38,14 @@ struct abg_graph {
   // (block-diagonal union); segment s owns U rows [seg_row0[s], +seg_n[s])
   int nseg = 1;
   std::vector<int64_t> seg_row0, seg_n;
-  // SpMM schedules: light rows in decreasing-degree order, heavy rows split
+  // SpMM schedules: light rows in tasks of consecutive rows, heavy rows split
   // into fixed-size edge chunks whose partial sums are reduced in order.
   struct Schedule {
-    int64_t n_light = 0;
-    int32_t* light = nullptr;        // row ids
+    int64_t n_tasks = 0;
+    int2* tasks = nullptr;           // light rows [x, y) of each task, consecutive and in order
+    int64_t n_etasks = 0, n_ztasks = 0;
+    int2* etasks = nullptr;          // the tasks that hold edges
+    int2* ztasks = nullptr;          // the tasks whose rows have no edges
     int64_t n_chunks = 0;
     int64_t* chunk_begin = nullptr;  // edge range of each chunk
     int32_t* chunk_row_slot = nullptr;  // heavy-row slot of each chunk
@@ -50,8 +53,9 @@ struct abg_graph {
     int32_t* heavy_row = nullptr;    // row id of each heavy slot
     int64_t* heavy_chunk0 = nullptr; // first chunk of each heavy slot (n_heavy + 1)
   } sched_u, sched_v;
+  int* wait_err = nullptr;  // device flag: a bounded wait inside a kernel ran out
   int64_t footprint = 0;
-  void* blocks[32] = {};
+  void* blocks[64] = {};
   int n_blocks = 0;
 };
 
@@ -60,7 +64,11 @@ namespace abg {
 constexpr int kMaxK = 128;     // clusters supported by the NCI kernels
 constexpr int kMaxD = 1024;    // feature width supported by the SpMMs
 constexpr int kHeavyChunk = 256;   // edges per chunk of a split row
-constexpr int kHeavyRow = 1024;    // rows with more edges are split
+constexpr int kHeavyRow = 256;     // rows with more edges are split
+constexpr int kTaskRows = 32;      // light rows per task, at most
+constexpr int kTaskEdges = 256;    // edges per task, at most (a light row has <= kHeavyRow)
+static_assert(kHeavyRow <= kTaskEdges && kTaskEdges % 4 == 0 && kTaskRows <= 32,
+              "task limits must fit the SpMM kernels' staging");
 
 // ---- graph.cu ---------------------------------------------------------------
 int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s);
@@ -70,6 +78,9 @@ int validate_desc(const abg_graph_desc* d);
 // ---- spmm.cu ----------------------------------------------------------------
 // Algorithm 1 propagation + Eq. 2 on device buffers. Exactly one of x_f32 /
 // x_bf16 is non-null (dense attributes, row stride ldx, width d).
+// Reads (and clears) the graph's wait flag after the stream's work: ABG_EDEVICE when a
+// bounded wait inside a kernel ran out. Synchronises s.
+int check_wait_flag(const abg_graph* g, cudaStream_t s);
 int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf16, int64_t ldx,
               int d, double alpha, int gamma, float* zhat, int64_t ldz, cudaStream_t s);
 // C[rows][ldc] = A_csr (rows x K) * B[K][ldb] (width n, plain sum per row).

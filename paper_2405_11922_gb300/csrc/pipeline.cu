@@ -314,6 +314,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     ABG_CUDA(cudaMemcpyAsync(cl.data(), o.clamped, sizeof(int) * nseg, cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaMemcpyAsync(&bd, o.breakdowns, sizeof(int), cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaStreamSynchronize(s));
+    ABG_TRY(check_wait_flag(g, s));
   }
   ABG_CUDA(cudaStreamSynchronize(s));
   ABG_CUDA(cudaGetLastError());
@@ -432,7 +433,10 @@ ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32
   ABG_CHECK(g && zhat, "null argument");
   ABG_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (x) return propagate(g, x, nullptr, ldx, d, alpha, gamma, zhat, ldz, s);
+  if (x) {
+    ABG_TRY(propagate(g, x, nullptr, ldx, d, alpha, gamma, zhat, ldz, s));
+    return check_wait_flag(g, s);
+  }
   ABG_CHECK(d == g->d_u, "x = NULL needs d == d_u");
   Scratch scr(s);
   RowSpace rs;
@@ -442,7 +446,8 @@ ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32
   int64_t lx;
   std::vector<uint64_t> seeds(g->nseg, 0);
   ABG_TRY(prepare_attributes(g, rs, d, 0, 0, seeds, scr, s, &xf, &xb, &lx, nullptr));
-  return propagate(g, xf, xb, lx, d, alpha, gamma, zhat, ldz, s);
+  ABG_TRY(propagate(g, xf, xb, lx, d, alpha, gamma, zhat, ldz, s));
+  return check_wait_flag(g, s);
 }
 
 ABG_API int abg_orthogonal_matrix(uint64_t seed, int32_t d, double* q_out, void* stream) {

@@ -7,10 +7,15 @@
 // float4 column chunks of that row, so one gathered input row is read with
 // G*V coalesced 16-byte loads. The group loads up to G (index, value) pairs
 // cooperatively, broadcasts them with shuffles and keeps 8 gathers in flight.
-// Light rows run in decreasing-degree order; rows with more than kHeavyRow
+// Light rows run as streaming tasks (runs of consecutive rows, at most
+// kTaskRows rows and about kTaskEdges edges); rows with more than kHeavyRow
 // edges are split into kHeavyChunk-edge chunks whose partial sums go to a
 // scratch buffer and are added back in chunk order, so results do not depend
 // on scheduling (no floating-point atomics).
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace abg {
@@ -101,10 +106,30 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int ch, int d) {
   return v;
 }
 
+// restart attributes of one row (modes 1/2), zero beyond column d
 template <int G, int V>
-__device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc_in)[V], float* C,
-                                               int64_t ldc, int nchunk, int lig, unsigned mask,
-                                               const EpiParams& ep) {
+__device__ __forceinline__ void load_x_row(int64_t row, int nchunk, int lig, const EpiParams& ep,
+                                           float4 (&xv)[V]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int ch = lig + G * v;
+    xv[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ep.mode != 0 && ch < nchunk) {
+      if (ep.x_bf16)
+        xv[v] = ld_bf16x4(reinterpret_cast<const __nv_bfloat16*>(ep.x) + row * ep.ldx + 4 * ch);
+      else
+        xv[v] = ld_nc_f4(reinterpret_cast<const float*>(ep.x) + row * ep.ldx + 4 * ch);
+      xv[v] = mask_tail(xv[v], ch, ep.d);
+    }
+  }
+}
+
+// C[row] = scale * acc (mode 0), c_x X[row] + c_p acc (mode 1), the same normalised (mode 2)
+template <int G, int V>
+__device__ __forceinline__ void epilogue_core(int64_t row, const float4 (&acc_in)[V],
+                                              const float4 (&xv)[V], float* C, int64_t ldc,
+                                              int nchunk, int lig, unsigned mask,
+                                              const EpiParams& ep) {
   float4 acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = mask_tail(acc_in[v], lig + G * v, ep.d);
@@ -118,22 +143,17 @@ __device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc_i
     float ss = 0.f;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      int ch = lig + G * v;
-      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (ch < nchunk) {
-        if (ep.x_bf16)
-          xv = ld_bf16x4(reinterpret_cast<const __nv_bfloat16*>(ep.x) + row * ep.ldx + 4 * ch);
-        else
-          xv = ld_nc_f4(reinterpret_cast<const float*>(ep.x) + row * ep.ldx + 4 * ch);
-        xv = mask_tail(xv, ch, ep.d);
-      }
       float4 z;
-      z.x = fmaf(ep.c_p, acc[v].x, ep.c_x * xv.x);
-      z.y = fmaf(ep.c_p, acc[v].y, ep.c_x * xv.y);
-      z.z = fmaf(ep.c_p, acc[v].z, ep.c_x * xv.z);
-      z.w = fmaf(ep.c_p, acc[v].w, ep.c_x * xv.w);
+      z.x = fmaf(ep.c_p, acc[v].x, ep.c_x * xv[v].x);
+      z.y = fmaf(ep.c_p, acc[v].y, ep.c_x * xv[v].y);
+      z.z = fmaf(ep.c_p, acc[v].z, ep.c_x * xv[v].z);
+      z.w = fmaf(ep.c_p, acc[v].w, ep.c_x * xv[v].w);
       out[v] = z;
-      ss += z.x * z.x + z.y * z.y + z.z * z.z + z.w * z.w;
+      // explicit FMAs: every inlined copy of this epilogue rounds the same way
+      ss = fmaf(z.x, z.x, ss);
+      ss = fmaf(z.y, z.y, ss);
+      ss = fmaf(z.z, z.z, ss);
+      ss = fmaf(z.w, z.w, ss);
     }
     if (ep.mode == 2) {
 #pragma unroll
@@ -155,6 +175,15 @@ __device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc_i
   }
 }
 
+template <int G, int V>
+__device__ __forceinline__ void epilogue_store(int64_t row, const float4 (&acc)[V], float* C,
+                                               int64_t ldc, int nchunk, int lig, unsigned mask,
+                                               const EpiParams& ep) {
+  float4 xv[V];
+  load_x_row<G, V>(row, nchunk, lig, ep, xv);
+  epilogue_core<G, V>(row, acc, xv, C, ldc, nchunk, lig, mask, ep);
+}
+
 // Light rows: one group per listed row (rows == nullptr: row = group index).
 template <int G, int V, class TIn>
 __global__ void __launch_bounds__(256) k_spmm_rows(const int32_t* __restrict__ rows, int64_t n_rows,
@@ -174,6 +203,328 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int32_t* __restrict__ r
   for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
   gather_range<G, V, TIn>(ptr[row], ptr[row + 1], col, val, B, ldb, nchunk, lig, mask, acc);
   epilogue_store<G, V>(row, acc, C, ldc, nchunk, lig, mask, ep);
+}
+
+// Light rows, streamed: one group per task, a run of consecutive light rows whose
+// edges are contiguous. The group walks the task's edge list G edges at a time,
+// keeping UNR gathers in flight across row boundaries, and finishes a row (epilogue)
+// when the edge cursor passes its end. Each row still sums its edges in edge
+// order, so results equal the one-row-per-group kernel.
+template <int G, int V, class TIn>
+__global__ void __launch_bounds__(256) k_spmm_stream(const int2* __restrict__ tasks,
+                                                     int64_t n_tasks,
+                                                     const int64_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const float* __restrict__ val,
+                                                     const TIn* __restrict__ B, int64_t ldb,
+                                                     float* __restrict__ C, int64_t ldc,
+                                                     int nchunk, EpiParams ep) {
+  constexpr int UNR = (V >= 4) ? 4 : (G < 8 ? G : 8);
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int lig = threadIdx.x & (G - 1);
+  if (grp >= n_tasks) return;  // whole groups exit together
+  const unsigned mask = group_mask<G>();
+  const int2 tk = tasks[grp];
+  const int64_t r0 = tk.x;
+  const int nrows = tk.y - tk.x;
+  const int64_t e_begin = ptr[r0];
+  const int64_t e_end = ptr[tk.y];
+  // lane i of the window holds the end of row wbase + i
+  int wbase = 0;
+  int64_t rp = lig < nrows ? ptr[r0 + 1 + lig] : e_end;
+  int cur = 0;
+  int64_t rend = __shfl_sync(mask, rp, 0, G);
+  float4 acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t base = e_begin; base < e_end; base += G) {
+    const int64_t j = base + lig;
+    int c = 0;
+    float w = 0.f;
+    if (j < e_end) {
+      c = __ldg(col + j);
+      w = __ldg(val + j);
+    }
+    const int64_t rem = e_end - base;
+    const int cnt = rem < G ? (int)rem : G;
+    for (int t = 0; t < cnt; t += UNR) {
+      float4 x[UNR][V];
+      float ws[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int src = (t + u) & (G - 1);
+        const int ct = __shfl_sync(mask, c, src, G);
+        ws[u] = __shfl_sync(mask, w, src, G);
+        const bool ok = (t + u) < cnt;
+        const TIn* rowp = B + (int64_t)ct * ldb;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int ch = lig + G * v;
+          x[u][v] = (ok && ch < nchunk) ? load4<TIn>(rowp + 4 * ch)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        if (t + u >= cnt) break;  // uniform over the group
+        const int64_t e = base + t + u;
+        while (e >= rend) {  // rows before the one edge e belongs to are complete
+          epilogue_store<G, V>(r0 + cur, acc, C, ldc, nchunk, lig, mask, ep);
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+          ++cur;  // stays < nrows: e < e_end, the end of the last row
+          if (cur - wbase >= G) {
+            wbase += G;
+            rp = wbase + lig < nrows ? ptr[r0 + 1 + wbase + lig] : e_end;
+          }
+          rend = __shfl_sync(mask, rp, cur - wbase, G);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = f4_fma(ws[u], x[u][v], acc[v]);
+      }
+    }
+  }
+  // the row holding the last edge, then the empty rows after it
+  for (; cur < nrows; ++cur) {
+    epilogue_store<G, V>(r0 + cur, acc, C, ldc, nchunk, lig, mask, ep);
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Light rows with TMA gathers (rows of at most 64 float4 chunks).
+//
+// One warp per task at a time, tasks gw, gw + W, ... of the warp's own list.
+// The task's (column, value) pairs are staged in shared memory; lane 0 issues
+// tile::gather4 copies (four gathered rows, one box row each) into a ring of
+// slots guarded by one mbarrier each, running up to `slots` groups ahead of
+// the consumer and at most one task ahead. All 32 lanes consume a slot in
+// edge order (lane c owns float4 chunk c (+32) of every row), so each output
+// row sums its edges in the same order as the other SpMM kernels. The restart
+// row of X is fetched when a row starts, so its latency hides behind the
+// row's gathers. Waits are bounded: a wait that runs out sets *wait_err,
+// drains this warp's copies (again bounded) and stops the warp.
+// ---------------------------------------------------------------------------
+constexpr int kTmaWarps = 12;           // warps (independent pipelines) per CTA
+constexpr int kTmaRingBytes = 8192;     // gather ring per warp
+constexpr uint64_t kTmaWaitNs = 1000000000ull;  // a wait longer than 1 s counts as failed
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait; false when it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kTmaWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int4 rows,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(rows.x), "r"(rows.y), "r"(rows.z),
+      "r"(rows.w), "r"(bar)
+      : "memory");
+}
+
+template <class TIn>
+__device__ __forceinline__ float4 smem_chunk(const unsigned char* row, int ch);
+template <>
+__device__ __forceinline__ float4 smem_chunk<float>(const unsigned char* row, int ch) {
+  return *reinterpret_cast<const float4*>(row + 16 * ch);
+}
+template <>
+__device__ __forceinline__ float4 smem_chunk<__nv_bfloat16>(const unsigned char* row, int ch) {
+  const uint2 u = *reinterpret_cast<const uint2*>(row + 8 * ch);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+struct TaskMeta {
+  int64_t r0;   // first row
+  int64_t e0;   // first edge
+  int nrows;
+  int ne;       // edges (>= 1)
+  int rend;     // this lane's row end (lane < nrows), relative to e0
+};
+
+template <int V, class TIn>
+__global__ void __launch_bounds__(kTmaWarps * 32, 1)
+    k_spmm_tma(const __grid_constant__ CUtensorMap bmap, const int2* __restrict__ tasks,
+               int64_t n_tasks, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+               const float* __restrict__ val, float* __restrict__ C, int64_t ldc, int nchunk,
+               int row_bytes, int slot_bytes, int slots, int warp_bytes, EpiParams ep,
+               int* __restrict__ wait_err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kTmaWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kTmaWarps;
+  if (gw >= n_tasks) return;  // whole warps; the kernel has no CTA-wide barrier
+  const int64_t n_mine = (n_tasks - gw + nw - 1) / nw;
+  unsigned char* ring = smem + (size_t)warp * warp_bytes;
+  int* idx = reinterpret_cast<int*>(ring + (size_t)slots * slot_bytes);  // [2][kTaskEdges]
+  float* wv = reinterpret_cast<float*>(idx + 2 * kTaskEdges);            // [2][kTaskEdges]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wv + 2 * kTaskEdges);      // [slots]
+  const uint32_t ring_s = smem_addr(ring);
+  const uint32_t bar_s = smem_addr(bars);
+  if (lane == 0)
+    for (int i = 0; i < slots; ++i) mbar_init(bar_s + 8 * i, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+
+  // task k of this warp: row range, edge range, row ends, staged (column, value) pairs
+  auto load_task = [&](int64_t k, TaskMeta& m) {
+    const int2 tk = tasks[gw + k * nw];
+    m.r0 = tk.x;
+    m.nrows = tk.y - tk.x;
+    m.e0 = ptr[tk.x];
+    m.ne = (int)(ptr[tk.y] - m.e0);
+    m.rend = lane < m.nrows ? (int)(ptr[tk.x + 1 + lane] - m.e0) : m.ne;
+    int* ib = idx + (k & 1) * kTaskEdges;
+    float* wb = wv + (k & 1) * kTaskEdges;
+    const int n4 = (m.ne + 3) & ~3;
+    for (int j = lane; j < n4; j += 32) {
+      const int jj = j < m.ne ? j : m.ne - 1;  // a padded slot re-gathers the last row
+      ib[j] = __ldg(col + m.e0 + jj);
+      wb[j] = j < m.ne ? __ldg(val + m.e0 + j) : 0.f;
+    }
+    __syncwarp();
+  };
+
+  TaskMeta mp, mc;
+  load_task(0, mp);
+  mc = mp;
+  int64_t pk = 0, ck = 0;  // producer / consumer task
+  int pg = 0, cg = 0;      // next group of the task to issue / consume
+  uint32_t g_issue = 0, g_cons = 0;
+  bool bad = false;
+
+  auto produce = [&]() -> bool {
+    if (pk >= n_mine) return false;
+    if (pg == ((mp.ne + 3) >> 2)) {
+      if (pk + 1 >= n_mine || pk + 1 > ck + 1) return false;
+      ++pk;
+      load_task(pk, mp);
+      pg = 0;
+    }
+    const int sl = (int)(g_issue % (uint32_t)slots);
+    if (lane == 0) {
+      const int4 rows = *reinterpret_cast<const int4*>(idx + (pk & 1) * kTaskEdges + 4 * pg);
+      const uint32_t bar = bar_s + 8 * sl;
+      mbar_expect_tx(bar, 4 * row_bytes);
+      tma_gather4(ring_s + sl * slot_bytes, &bmap, rows, bar);
+    }
+    ++pg;
+    ++g_issue;
+    return true;
+  };
+
+  float4 acc[V], xv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int cur = 0;
+  int rend = __shfl_sync(0xffffffffu, mc.rend, 0);
+  load_x_row<32, V>(mc.r0, nchunk, lane, ep, xv);
+
+  while (ck < n_mine) {
+    while (g_issue < g_cons + (uint32_t)slots && produce()) {
+    }
+    const int sl = (int)(g_cons % (uint32_t)slots);
+    bad = !mbar_wait_bounded(bar_s + 8 * sl, (g_cons / (uint32_t)slots) & 1u);
+    if (__any_sync(0xffffffffu, bad)) {
+      bad = true;
+      break;
+    }
+    const unsigned char* slot = ring + (size_t)sl * slot_bytes;
+    const float* wb = wv + (ck & 1) * kTaskEdges;
+    if (4 * cg + 4 <= rend) {  // common case: the four edges lie in the current row
+      const float4 w4 = *reinterpret_cast<const float4*>(wb + 4 * cg);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int ch = lane + 32 * v;
+        if (ch < nchunk) {
+          acc[v] = f4_fma(w4.x, smem_chunk<TIn>(slot, ch), acc[v]);
+          acc[v] = f4_fma(w4.y, smem_chunk<TIn>(slot + row_bytes, ch), acc[v]);
+          acc[v] = f4_fma(w4.z, smem_chunk<TIn>(slot + 2 * row_bytes, ch), acc[v]);
+          acc[v] = f4_fma(w4.w, smem_chunk<TIn>(slot + 3 * row_bytes, ch), acc[v]);
+        }
+      }
+    } else
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * cg + i;
+      if (j >= mc.ne) break;  // uniform
+      while (j >= rend) {     // rows ending before edge j are complete
+        epilogue_core<32, V>(mc.r0 + cur, acc, xv, C, ldc, nchunk, lane, 0xffffffffu, ep);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ++cur;  // < nrows: j < ne, the end of the last row
+        rend = __shfl_sync(0xffffffffu, mc.rend, cur);
+        load_x_row<32, V>(mc.r0 + cur, nchunk, lane, ep, xv);
+      }
+      const float w = wb[j];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int ch = lane + 32 * v;
+        if (ch < nchunk) acc[v] = f4_fma(w, smem_chunk<TIn>(slot + i * row_bytes, ch), acc[v]);
+      }
+    }
+    __syncwarp();  // the slot is free once every lane has read it
+    ++g_cons;
+    ++cg;
+    if (cg == ((mc.ne + 3) >> 2)) {
+      // the row holding the task's last edge, then the empty rows after it
+      for (; cur < mc.nrows; ++cur) {
+        epilogue_core<32, V>(mc.r0 + cur, acc, xv, C, ldc, nchunk, lane, 0xffffffffu, ep);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cur + 1 < mc.nrows) load_x_row<32, V>(mc.r0 + cur + 1, nchunk, lane, ep, xv);
+      }
+      ++ck;
+      cg = 0;
+      if (ck < n_mine) {
+        while (pk < ck && produce()) {
+        }
+        mc = mp;  // pk == ck: the producer has staged task ck
+        cur = 0;
+        rend = __shfl_sync(0xffffffffu, mc.rend, 0);
+        load_x_row<32, V>(mc.r0, nchunk, lane, ep, xv);
+      }
+    }
+  }
+  if (bad) {
+    if (lane == 0) atomicExch(wait_err, 1);
+    for (uint32_t g = g_cons; g < g_issue; ++g)  // copies still in flight into this ring
+      if (!mbar_wait_bounded(bar_s + 8 * (g % (uint32_t)slots), (g / (uint32_t)slots) & 1u)) break;
+  }
 }
 
 // Heavy rows, phase 1: one group per chunk, raw partial sums.
@@ -267,12 +618,87 @@ static inline unsigned blocks_for(int64_t groups, int G) {
   return (unsigned)ceil_div(groups * G, 256);
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Light tasks with edges through k_spmm_tma; *used stays false when the shape does not
+// fit its limits (row box of at most 256 elements, 16-byte rows and base).
+template <int V, class TIn>
+static int run_spmm_tma(const abg_graph::Schedule& sc, const int64_t* ptr, const int32_t* col,
+                        const float* val, const TIn* B, int64_t ldb, int64_t b_rows, float* C,
+                        int64_t ldc, int nchunk, const EpiParams& ep, int* wait_err,
+                        cudaStream_t s, bool* used) {
+  *used = false;
+  if (sc.n_etasks == 0 || !wait_err) return ABG_OK;
+  const auto enc = tensor_map_encoder();
+  const int box_w = 4 * nchunk;
+  const int row_bytes = box_w * (int)sizeof(TIn);
+  const int64_t stride = ldb * (int64_t)sizeof(TIn);
+  if (!enc || b_rows < 1 || b_rows > INT32_MAX || box_w > 256 || stride % 16 != 0 ||
+      row_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(B) % 16 != 0)
+    return ABG_OK;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)box_w, (cuuint64_t)b_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, 1};  // one row per box: gather4 fetches four
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r =
+      enc(&map, sizeof(TIn) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+          2, const_cast<TIn*>(B), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return ABG_OK;
+  const int slot_bytes = (int)round_up(4 * row_bytes, 128);
+  const int slots = std::max(2, std::min(32, kTmaRingBytes / slot_bytes));
+  const int warp_bytes = (int)round_up(slots * slot_bytes + 4 * kTaskEdges * 4 + slots * 8, 1024);
+  const size_t smem = (size_t)kTmaWarps * warp_bytes;
+  if (smem > 220 * 1024) return ABG_OK;
+  ABG_TRY(raise_smem_limit((const void*)k_spmm_tma<V, TIn>, smem));
+  const int64_t blocks = std::min<int64_t>(ceil_div(sc.n_etasks, kTmaWarps), num_sms());
+  k_spmm_tma<V, TIn><<<(unsigned)blocks, kTmaWarps * 32, smem, s>>>(
+      map, sc.etasks, sc.n_etasks, ptr, col, val, C, ldc, nchunk, row_bytes, slot_bytes, slots,
+      warp_bytes, ep, wait_err);
+  ::abg::note_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
 template <int G, int V, class TIn>
 static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t n_rows,
                     const int64_t* ptr, const int32_t* col, const float* val, const TIn* B,
-                    int64_t ldb, float* C, int64_t ldc, int nchunk, const EpiParams& ep,
-                    float* part, int64_t ldp, cudaStream_t s) {
-  if (n_rows > 0) {
+                    int64_t ldb, int64_t b_rows, float* C, int64_t ldc, int nchunk,
+                    const EpiParams& ep, float* part, int64_t ldp, int* wait_err, cudaStream_t s) {
+  bool tma = false;
+  if constexpr (G == 32 && V <= 2) {
+    if (sc) {
+      const int st = run_spmm_tma<V, TIn>(*sc, ptr, col, val, B, ldb, b_rows, C, ldc, nchunk, ep,
+                                          wait_err, s, &tma);
+      if (st != ABG_OK) return st;
+    }
+  }
+  if (tma) {
+    if (sc->n_ztasks > 0) {
+      k_spmm_stream<G, V, TIn><<<blocks_for(sc->n_ztasks, G), 256, 0, s>>>(
+          sc->ztasks, sc->n_ztasks, ptr, col, val, B, ldb, C, ldc, nchunk, ep); ::abg::note_launch();
+    }
+  } else if (sc && sc->n_tasks > 0) {
+    k_spmm_stream<G, V, TIn><<<blocks_for(sc->n_tasks, G), 256, 0, s>>>(
+        sc->tasks, sc->n_tasks, ptr, col, val, B, ldb, C, ldc, nchunk, ep); ::abg::note_launch();
+  } else if (!sc && n_rows > 0) {
     k_spmm_rows<G, V, TIn><<<blocks_for(n_rows, G), 256, 0, s>>>(rows, n_rows, ptr, col, val, B,
                                                                  ldb, C, ldc, nchunk, ep); ::abg::note_launch();
   }
@@ -290,13 +716,14 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
 template <class TIn>
 static int dispatch_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t n_rows,
                          const int64_t* ptr, const int32_t* col, const float* val, const TIn* B,
-                         int64_t ldb, float* C, int64_t ldc, int nchunk, const EpiParams& ep,
-                         float* part, int64_t ldp, cudaStream_t s) {
+                         int64_t ldb, int64_t b_rows, float* C, int64_t ldc, int nchunk,
+                         const EpiParams& ep, float* part, int64_t ldp, int* wait_err,
+                         cudaStream_t s) {
   Shape sh = shape_for(nchunk);
-#define ABG_SPMM_CASE(g, v)                                                                      \
-  if (sh.G == g && sh.V == v)                                                                    \
-    return run_spmm<g, v, TIn>(sc, rows, n_rows, ptr, col, val, B, ldb, C, ldc, nchunk, ep, part, \
-                               ldp, s);
+#define ABG_SPMM_CASE(g, v)                                                                     \
+  if (sh.G == g && sh.V == v)                                                                   \
+    return run_spmm<g, v, TIn>(sc, rows, n_rows, ptr, col, val, B, ldb, b_rows, C, ldc, nchunk, \
+                               ep, part, ldp, wait_err, s);
   ABG_SPMM_CASE(4, 1)
   ABG_SPMM_CASE(8, 1)
   ABG_SPMM_CASE(16, 1)
@@ -354,34 +781,44 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
     if (it == 0) {
       EpiParams ep{0, (float)(1.0 - alpha), 0.f, 0.f, nullptr, 0, 0, d};
       if (x_bf16)
-        ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, g->sched_v.light, g->sched_v.n_light,
-                                             g->v_ptr, g->v_col, g->v_val, x_bf16, ldx, W, ldw,
-                                             nchunk, ep, part, ldw, s));
+        ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col,
+                                             g->v_val, x_bf16, ldx, g->n_u, W, ldw, nchunk, ep,
+                                             part, ldw, g->wait_err, s));
       else
-        ABG_TRY(dispatch_spmm<float>(&g->sched_v, g->sched_v.light, g->sched_v.n_light, g->v_ptr,
-                                     g->v_col, g->v_val, x_f32, ldx, W, ldw, nchunk, ep, part,
-                                     ldw, s));
+        ABG_TRY(dispatch_spmm<float>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val,
+                                     x_f32, ldx, g->n_u, W, ldw, nchunk, ep, part, ldw,
+                                     g->wait_err, s));
     } else {
       EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0, d};
-      ABG_TRY(dispatch_spmm<float>(&g->sched_v, g->sched_v.light, g->sched_v.n_light, g->v_ptr,
-                                   g->v_col, g->v_val, zhat, ldz, W, ldw, nchunk, ep, part, ldw,
-                                   s));
+      ABG_TRY(dispatch_spmm<float>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val, zhat,
+                                   ldz, g->n_u, W, ldw, nchunk, ep, part, ldw, g->wait_err, s));
     }
     // Z = (1-a) X + a L W   (+ Eq. 2 on the last round)
     EpiParams ep = ep_restart;
     ep.mode = (it == gamma - 1) ? 2 : 1;
-    ABG_TRY(dispatch_spmm<float>(&g->sched_u, g->sched_u.light, g->sched_u.n_light, g->u_ptr,
-                                 g->u_col, g->u_val, W, ldw, zhat, ldz, nchunk, ep, part, ldw, s));
+    ABG_TRY(dispatch_spmm<float>(&g->sched_u, nullptr, 0, g->u_ptr, g->u_col, g->u_val, W, ldw,
+                                 g->n_v, zhat, ldz, nchunk, ep, part, ldw, g->wait_err, s));
   }
   return ABG_OK;
+}
+
+int check_wait_flag(const abg_graph* g, cudaStream_t s) {
+  int flag = 0;
+  ABG_CUDA(cudaMemcpyAsync(&flag, g->wait_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  if (flag == 0) return ABG_OK;
+  ABG_CUDA(cudaMemsetAsync(g->wait_err, 0, sizeof(int), s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  set_error("a bounded wait in the SpMM gather pipeline ran out; its results are invalid");
+  return ABG_EDEVICE;
 }
 
 int spmm_plain(const int64_t* ptr, const int32_t* col, const float* val, int64_t rows,
                const float* B, int64_t ldb, int n, float* C, int64_t ldc, cudaStream_t s) {
   ABG_CHECK(n >= 1 && n <= kMaxD, "spmm: width out of range");
   EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0, n};
-  return dispatch_spmm<float>(nullptr, nullptr, rows, ptr, col, val, B, ldb, C, ldc, (n + 3) / 4,
-                              ep, nullptr, 0, s);
+  return dispatch_spmm<float>(nullptr, nullptr, rows, ptr, col, val, B, ldb, 0, C, ldc,
+                              (n + 3) / 4, ep, nullptr, 0, nullptr, s);
 }
 
 __global__ void k_csr_to_dense(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,

@@ -57,6 +57,14 @@ GRAPHS = {
     "csr_x": lambda: synth.make_small(4, n_u=150, n_v=170, k=3, d_u=24, x_kind="csr_f32"),
     "heavy": lambda: synth.make_config3(scale=0.005, k=10),
     "wide": lambda: synth.make_small(5, n_u=160, n_v=200, k=3, d_u=300, deg=8),
+    # rows of 17..64 float4 chunks take the TMA-gather kernel: f32 and bf16 rows, one and two
+    # chunks per lane, runs of isolated rows (tasks without edges), several tasks per warp
+    "gather_f32": lambda: synth.make_small(10, n_u=3000, n_v=4100, k=4, d_u=100, deg=9,
+                                           isolated_u=70, isolated_v=90),
+    "gather_bf16": lambda: synth.make_small(11, n_u=2500, n_v=3000, k=4, d_u=72, deg=6,
+                                            x_kind="dense_bf16", isolated_u=40),
+    "gather_wide": lambda: synth.make_small(12, n_u=1200, n_v=1500, k=3, d_u=200, deg=7,
+                                            isolated_v=50),
 }
 
 
