@@ -375,9 +375,18 @@ struct TaskMeta {
   int rend;     // this lane's row end (lane < nrows), relative to e0
 };
 
-template <int V, class TIn>
+// Work items of k_spmm_tma: light tasks (row ranges), or the chunks of heavy rows
+// (CHUNK: item c sums kHeavyChunk edges of one row into row c of the partial buffer).
+struct TmaItems {
+  const int2* tasks;
+  const int64_t* chunk_begin;
+  const int32_t* chunk_slot;
+  const int32_t* heavy_row;
+};
+
+template <int V, class TIn, bool CHUNK>
 __global__ void __launch_bounds__(kTmaWarps * 32, 1)
-    k_spmm_tma(const __grid_constant__ CUtensorMap bmap, const int2* __restrict__ tasks,
+    k_spmm_tma(const __grid_constant__ CUtensorMap bmap, const TmaItems items,
                int64_t n_tasks, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                const float* __restrict__ val, float* __restrict__ C, int64_t ldc, int nchunk,
                int row_bytes, int slot_bytes, int slots, int warp_bytes, EpiParams ep,
@@ -402,12 +411,23 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
 
   // task k of this warp: row range, edge range, row ends, staged (column, value) pairs
   auto load_task = [&](int64_t k, TaskMeta& m) {
-    const int2 tk = tasks[gw + k * nw];
-    m.r0 = tk.x;
-    m.nrows = tk.y - tk.x;
-    m.e0 = ptr[tk.x];
-    m.ne = (int)(ptr[tk.y] - m.e0);
-    m.rend = lane < m.nrows ? (int)(ptr[tk.x + 1 + lane] - m.e0) : m.ne;
+    if constexpr (CHUNK) {
+      const int64_t c = gw + k * nw;
+      const int64_t row = items.heavy_row[items.chunk_slot[c]];
+      m.r0 = c;
+      m.nrows = 1;
+      m.e0 = items.chunk_begin[c];
+      const int64_t rest = ptr[row + 1] - m.e0;
+      m.ne = rest < kHeavyChunk ? (int)rest : kHeavyChunk;
+      m.rend = m.ne;
+    } else {
+      const int2 tk = items.tasks[gw + k * nw];
+      m.r0 = tk.x;
+      m.nrows = tk.y - tk.x;
+      m.e0 = ptr[tk.x];
+      m.ne = (int)(ptr[tk.y] - m.e0);
+      m.rend = lane < m.nrows ? (int)(ptr[tk.x + 1 + lane] - m.e0) : m.ne;
+    }
     int* ib = idx + (k & 1) * kTaskEdges;
     float* wb = wv + (k & 1) * kTaskEdges;
     const int n4 = (m.ne + 3) & ~3;
@@ -567,12 +587,33 @@ __global__ void __launch_bounds__(256) k_spmm_reduce(const int32_t* __restrict__
   float4 acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t c = heavy_chunk0[grp]; c < heavy_chunk0[grp + 1]; ++c) {
+  const int64_t c1 = heavy_chunk0[grp + 1];
+  int64_t c = heavy_chunk0[grp];
+  // partials added in chunk order; eight loads in flight at a time
+  for (; c + 8 <= c1; c += 8) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      int ch = lig + G * v;
+      const int ch = lig + G * v;
       if (ch < nchunk) {
-        float4 p = ld_f4(part + c * ldp + 4 * ch);
+        float4 p[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) p[u] = ld_f4(part + (c + u) * ldp + 4 * ch);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc[v].x += p[u].x;
+          acc[v].y += p[u].y;
+          acc[v].z += p[u].z;
+          acc[v].w += p[u].w;
+        }
+      }
+    }
+  }
+  for (; c < c1; ++c) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int ch = lig + G * v;
+      if (ch < nchunk) {
+        const float4 p = ld_f4(part + c * ldp + 4 * ch);
         acc[v].x += p.x;
         acc[v].y += p.y;
         acc[v].z += p.z;
@@ -639,10 +680,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 template <int V, class TIn>
 static int run_spmm_tma(const abg_graph::Schedule& sc, const int64_t* ptr, const int32_t* col,
                         const float* val, const TIn* B, int64_t ldb, int64_t b_rows, float* C,
-                        int64_t ldc, int nchunk, const EpiParams& ep, int* wait_err,
-                        cudaStream_t s, bool* used) {
+                        int64_t ldc, int nchunk, const EpiParams& ep, float* part, int64_t ldp,
+                        int* wait_err, cudaStream_t s, bool* used) {
   *used = false;
-  if (sc.n_etasks == 0 || !wait_err) return ABG_OK;
+  if (sc.n_etasks + sc.n_chunks == 0 || !wait_err) return ABG_OK;
   const auto enc = tensor_map_encoder();
   const int box_w = 4 * nchunk;
   const int row_bytes = box_w * (int)sizeof(TIn);
@@ -666,12 +707,24 @@ static int run_spmm_tma(const abg_graph::Schedule& sc, const int64_t* ptr, const
   const int warp_bytes = (int)round_up(slots * slot_bytes + 4 * kTaskEdges * 4 + slots * 8, 1024);
   const size_t smem = (size_t)kTmaWarps * warp_bytes;
   if (smem > 220 * 1024) return ABG_OK;
-  ABG_TRY(raise_smem_limit((const void*)k_spmm_tma<V, TIn>, smem));
-  const int64_t blocks = std::min<int64_t>(ceil_div(sc.n_etasks, kTmaWarps), num_sms());
-  k_spmm_tma<V, TIn><<<(unsigned)blocks, kTmaWarps * 32, smem, s>>>(
-      map, sc.etasks, sc.n_etasks, ptr, col, val, C, ldc, nchunk, row_bytes, slot_bytes, slots,
-      warp_bytes, ep, wait_err);
-  ::abg::note_launch();
+  ABG_TRY(raise_smem_limit((const void*)k_spmm_tma<V, TIn, false>, smem));
+  ABG_TRY(raise_smem_limit((const void*)k_spmm_tma<V, TIn, true>, smem));
+  const TmaItems items{sc.etasks, sc.chunk_begin, sc.chunk_row_slot, sc.heavy_row};
+  if (sc.n_chunks > 0) {  // raw partial sums of the heavy rows' chunks
+    const EpiParams raw{0, 1.f, 0.f, 0.f, nullptr, 0, 0, ep.d};
+    const int64_t blocks = std::min<int64_t>(ceil_div(sc.n_chunks, kTmaWarps), num_sms());
+    k_spmm_tma<V, TIn, true><<<(unsigned)blocks, kTmaWarps * 32, smem, s>>>(
+        map, items, sc.n_chunks, ptr, col, val, part, ldp, nchunk, row_bytes, slot_bytes, slots,
+        warp_bytes, raw, wait_err);
+    ::abg::note_launch();
+  }
+  if (sc.n_etasks > 0) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(sc.n_etasks, kTmaWarps), num_sms());
+    k_spmm_tma<V, TIn, false><<<(unsigned)blocks, kTmaWarps * 32, smem, s>>>(
+        map, items, sc.n_etasks, ptr, col, val, C, ldc, nchunk, row_bytes, slot_bytes, slots,
+        warp_bytes, ep, wait_err);
+    ::abg::note_launch();
+  }
   ABG_LAUNCH_CHECK();
   *used = true;
   return ABG_OK;
@@ -686,7 +739,7 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
   if constexpr (G == 32 && V <= 2) {
     if (sc) {
       const int st = run_spmm_tma<V, TIn>(*sc, ptr, col, val, B, ldb, b_rows, C, ldc, nchunk, ep,
-                                          wait_err, s, &tma);
+                                          part, ldp, wait_err, s, &tma);
       if (st != ABG_OK) return st;
     }
   }
@@ -703,9 +756,11 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
                                                                  ldb, C, ldc, nchunk, ep); ::abg::note_launch();
   }
   if (sc && sc->n_chunks > 0) {
-    k_spmm_chunks<G, V, TIn><<<blocks_for(sc->n_chunks, G), 256, 0, s>>>(
-        sc->chunk_begin, sc->chunk_row_slot, sc->heavy_row, sc->n_chunks, ptr, col, val, B, ldb,
-        part, ldp, nchunk); ::abg::note_launch();
+    if (!tma) {
+      k_spmm_chunks<G, V, TIn><<<blocks_for(sc->n_chunks, G), 256, 0, s>>>(
+          sc->chunk_begin, sc->chunk_row_slot, sc->heavy_row, sc->n_chunks, ptr, col, val, B, ldb,
+          part, ldp, nchunk); ::abg::note_launch();
+    }
     k_spmm_reduce<G, V><<<blocks_for(sc->n_heavy, G), 256, 0, s>>>(
         sc->heavy_row, sc->heavy_chunk0, sc->n_heavy, part, ldp, C, ldc, nchunk, ep); ::abg::note_launch();
   }
