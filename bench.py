@@ -298,7 +298,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                               "objective"], phase_ms)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "propagation SpMMs (k_spmm_stream/chunks/reduce, gamma rounds)",
+                     "kernel": "propagation SpMMs (k_spmm_tma light tasks + heavy chunks, k_spmm_reduce; gamma rounds)",
                      "peak_kind": peak_kind},
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},

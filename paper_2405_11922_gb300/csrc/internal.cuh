@@ -63,10 +63,13 @@ namespace abg {
 
 constexpr int kMaxK = 128;     // clusters supported by the NCI kernels
 constexpr int kMaxD = 1024;    // feature width supported by the SpMMs
-constexpr int kHeavyChunk = 256;   // edges per chunk of a split row
-constexpr int kHeavyRow = 256;     // rows with more edges are split
-constexpr int kTaskRows = 32;      // light rows per task, at most
-constexpr int kTaskEdges = 256;    // edges per task, at most (a light row has <= kHeavyRow)
+#ifndef ABG_TASK_EDGES
+#define ABG_TASK_EDGES 128
+#endif
+constexpr int kHeavyChunk = ABG_TASK_EDGES;  // edges per chunk of a split row
+constexpr int kHeavyRow = ABG_TASK_EDGES;    // rows with more edges are split
+constexpr int kTaskRows = 32;                // light rows per task, at most
+constexpr int kTaskEdges = ABG_TASK_EDGES;   // edges per task, at most (light rows: <= kHeavyRow)
 static_assert(kHeavyRow <= kTaskEdges && kTaskEdges % 4 == 0 && kTaskRows <= 32,
               "task limits must fit the SpMM kernels' staging");
 

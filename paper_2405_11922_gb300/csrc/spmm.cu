@@ -293,6 +293,126 @@ __global__ void __launch_bounds__(256) k_spmm_stream(const int2* __restrict__ ta
 }
 
 // ---------------------------------------------------------------------------
+// Light tasks (or heavy-row chunks) for rows of 17..64 float4 chunks: one warp
+// per work item, lane c owning chunk c (+32). Edge indices are relative to the
+// item's first edge (32-bit); the (column, value) pairs of the next 32 edges
+// are fetched while the current 32 are gathered, UNR row gathers are in flight
+// per step, a step whose UNR edges lie in the current row skips the boundary
+// checks, and the restart row of X is fetched when a row starts. Each row sums
+// its edges in edge order, as in the other SpMM kernels.
+// CHUNK: item c sums the kHeavyChunk edges of chunk c into row c of `C` (the
+// partial buffer) with the raw epilogue.
+// ---------------------------------------------------------------------------
+struct SpmmItems {
+  const int2* tasks;
+  const int64_t* chunk_begin;
+  const int32_t* chunk_slot;
+  const int32_t* heavy_row;
+};
+
+template <int V, class TIn, bool CHUNK, int MODE, int UNR, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_spmm_warp(const SpmmItems items, int64_t n_items, const int64_t* __restrict__ ptr,
+                const int32_t* __restrict__ col, const float* __restrict__ val,
+                const TIn* __restrict__ B, int ldb, float* __restrict__ C, int ldc, int nchunk,
+                EpiParams ep) {
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= n_items) return;  // whole warps
+  ep.mode = MODE;  // a compile-time mode lets the compiler drop the other epilogues
+  int64_t r0, e0;
+  int nrows, ne, rend_l;
+  if constexpr (CHUNK) {
+    const int64_t row = items.heavy_row[items.chunk_slot[item]];
+    r0 = item;
+    nrows = 1;
+    e0 = items.chunk_begin[item];
+    const int64_t rest = ptr[row + 1] - e0;
+    ne = rest < kHeavyChunk ? (int)rest : kHeavyChunk;
+    rend_l = ne;
+  } else {
+    const int2 tk = items.tasks[item];
+    r0 = tk.x;
+    nrows = tk.y - tk.x;
+    e0 = ptr[tk.x];
+    ne = (int)(ptr[tk.y] - e0);
+    rend_l = lane < nrows ? (int)(ptr[tk.x + 1 + lane] - e0) : ne;
+  }
+  const int32_t* __restrict__ colp = col + e0;
+  const float* __restrict__ valp = val + e0;
+  float4 acc[V], xv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  load_x_row<32, V>(r0, nchunk, lane, ep, xv);
+  int cur = 0;
+  int rend = __shfl_sync(0xffffffffu, rend_l, 0);
+  int c_next = lane < ne ? __ldg(colp + lane) : 0;
+  float w_next = lane < ne ? __ldg(valp + lane) : 0.f;
+  for (int base = 0; base < ne; base += 32) {
+    const int c = c_next;
+    const float w = w_next;
+    if (base + 32 + lane < ne) {  // the next 32 pairs, fetched while these are gathered
+      c_next = __ldg(colp + base + 32 + lane);
+      w_next = __ldg(valp + base + 32 + lane);
+    }
+    const int cnt = ne - base < 32 ? ne - base : 32;
+    for (int t = 0; t < cnt; t += UNR) {
+      float4 x[UNR][V];
+      float ws[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int src = t + u;
+        const int ct = __shfl_sync(0xffffffffu, c, src & 31);
+        ws[u] = __shfl_sync(0xffffffffu, w, src & 31);
+        const TIn* rowp = B + (int64_t)ct * ldb;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int ch = lane + 32 * v;
+          x[u][v] = (src < cnt && ch < nchunk) ? load4<TIn>(rowp + 4 * ch)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      if (base + t + UNR <= rend) {  // all UNR edges in the current row
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] = f4_fma(ws[u], x[u][v], acc[v]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int e = base + t + u;
+          if (e >= ne) break;  // uniform
+          while (e >= rend) {  // rows ending before edge e are complete
+            epilogue_core<32, V>(r0 + cur, acc, xv, C, ldc, nchunk, lane, 0xffffffffu, ep);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ++cur;  // < nrows: e < ne, the end of the last row
+            rend = __shfl_sync(0xffffffffu, rend_l, cur);
+            load_x_row<32, V>(r0 + cur, nchunk, lane, ep, xv);
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v] = f4_fma(ws[u], x[u][v], acc[v]);
+        }
+      }
+    }
+  }
+  // the row holding the last edge, then the empty rows after it
+  for (; cur < nrows; ++cur) {
+    epilogue_core<32, V>(r0 + cur, acc, xv, C, ldc, nchunk, lane, 0xffffffffu, ep);
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (cur + 1 < nrows) load_x_row<32, V>(r0 + cur + 1, nchunk, lane, ep, xv);
+  }
+}
+
+#ifndef ABG_WARP_UNR
+#define ABG_WARP_UNR 4
+#endif
+#ifndef ABG_WARP_MINB
+#define ABG_WARP_MINB 5
+#endif
+
+// ---------------------------------------------------------------------------
 // Light rows with TMA gathers (rows of at most 64 float4 chunks).
 //
 // One warp per task at a time, tasks gw, gw + W, ... of the warp's own list.
@@ -306,8 +426,14 @@ __global__ void __launch_bounds__(256) k_spmm_stream(const int2* __restrict__ ta
 // row's gathers. Waits are bounded: a wait that runs out sets *wait_err,
 // drains this warp's copies (again bounded) and stops the warp.
 // ---------------------------------------------------------------------------
-constexpr int kTmaWarps = 12;           // warps (independent pipelines) per CTA
-constexpr int kTmaRingBytes = 8192;     // gather ring per warp
+#ifndef ABG_TMA_WARPS
+#define ABG_TMA_WARPS 28
+#endif
+#ifndef ABG_TMA_RING
+#define ABG_TMA_RING 4096
+#endif
+constexpr int kTmaWarps = ABG_TMA_WARPS;     // warps (independent pipelines) per CTA
+constexpr int kTmaRingBytes = ABG_TMA_RING;  // gather ring per warp
 constexpr uint64_t kTmaWaitNs = 1000000000ull;  // a wait longer than 1 s counts as failed
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -444,7 +570,10 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
   mc = mp;
   int64_t pk = 0, ck = 0;  // producer / consumer task
   int pg = 0, cg = 0;      // next group of the task to issue / consume
-  uint32_t g_issue = 0, g_cons = 0;
+  int inflight = 0;        // groups issued and not yet consumed
+  int p_slot = 0;          // ring slot of the next issue
+  int c_slot = 0;          // ring slot of the next group to consume, and its phase parity
+  uint32_t c_phase = 0;
   bool bad = false;
 
   auto produce = [&]() -> bool {
@@ -455,15 +584,15 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
       load_task(pk, mp);
       pg = 0;
     }
-    const int sl = (int)(g_issue % (uint32_t)slots);
     if (lane == 0) {
       const int4 rows = *reinterpret_cast<const int4*>(idx + (pk & 1) * kTaskEdges + 4 * pg);
-      const uint32_t bar = bar_s + 8 * sl;
+      const uint32_t bar = bar_s + 8 * p_slot;
       mbar_expect_tx(bar, 4 * row_bytes);
-      tma_gather4(ring_s + sl * slot_bytes, &bmap, rows, bar);
+      tma_gather4(ring_s + p_slot * slot_bytes, &bmap, rows, bar);
     }
     ++pg;
-    ++g_issue;
+    ++inflight;
+    p_slot = p_slot + 1 == slots ? 0 : p_slot + 1;
     return true;
   };
 
@@ -475,10 +604,10 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
   load_x_row<32, V>(mc.r0, nchunk, lane, ep, xv);
 
   while (ck < n_mine) {
-    while (g_issue < g_cons + (uint32_t)slots && produce()) {
+    while (inflight < slots && produce()) {
     }
-    const int sl = (int)(g_cons % (uint32_t)slots);
-    bad = !mbar_wait_bounded(bar_s + 8 * sl, (g_cons / (uint32_t)slots) & 1u);
+    const int sl = c_slot;
+    bad = !mbar_wait_bounded(bar_s + 8 * sl, c_phase);
     if (__any_sync(0xffffffffu, bad)) {
       bad = true;
       break;
@@ -518,7 +647,11 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
       }
     }
     __syncwarp();  // the slot is free once every lane has read it
-    ++g_cons;
+    --inflight;
+    if (++c_slot == slots) {
+      c_slot = 0;
+      c_phase ^= 1u;
+    }
     ++cg;
     if (cg == ((mc.ne + 3) >> 2)) {
       // the row holding the task's last edge, then the empty rows after it
@@ -542,8 +675,13 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1)
   }
   if (bad) {
     if (lane == 0) atomicExch(wait_err, 1);
-    for (uint32_t g = g_cons; g < g_issue; ++g)  // copies still in flight into this ring
-      if (!mbar_wait_bounded(bar_s + 8 * (g % (uint32_t)slots), (g / (uint32_t)slots) & 1u)) break;
+    for (; inflight > 0; --inflight) {  // copies still in flight into this ring
+      if (!mbar_wait_bounded(bar_s + 8 * c_slot, c_phase)) break;
+      if (++c_slot == slots) {
+        c_slot = 0;
+        c_phase ^= 1u;
+      }
+    }
   }
 }
 
@@ -735,12 +873,36 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
                     const int64_t* ptr, const int32_t* col, const float* val, const TIn* B,
                     int64_t ldb, int64_t b_rows, float* C, int64_t ldc, int nchunk,
                     const EpiParams& ep, float* part, int64_t ldp, int* wait_err, cudaStream_t s) {
-  bool tma = false;
+  bool tma = false;  // light tasks with edges and the heavy chunks are done
   if constexpr (G == 32 && V <= 2) {
     if (sc) {
       const int st = run_spmm_tma<V, TIn>(*sc, ptr, col, val, B, ldb, b_rows, C, ldc, nchunk, ep,
                                           part, ldp, wait_err, s, &tma);
       if (st != ABG_OK) return st;
+    }
+    if (sc && !tma) {  // the TMA path declined this shape: register gathers, one warp per item
+      constexpr int U = ABG_WARP_UNR, MB = ABG_WARP_MINB;
+      const SpmmItems items{sc->etasks, sc->chunk_begin, sc->chunk_row_slot, sc->heavy_row};
+      if (sc->n_chunks > 0) {
+        const EpiParams raw{0, 1.f, 0.f, 0.f, nullptr, 0, 0, ep.d};
+        k_spmm_warp<V, TIn, true, 0, U, MB><<<(unsigned)ceil_div(sc->n_chunks, 8), 256, 0, s>>>(
+            items, sc->n_chunks, ptr, col, val, B, (int)ldb, part, (int)ldp, nchunk, raw);
+        ::abg::note_launch();
+      }
+      if (sc->n_etasks > 0) {
+        const unsigned grid = (unsigned)ceil_div(sc->n_etasks, 8);
+        if (ep.mode == 0)
+          k_spmm_warp<V, TIn, false, 0, U, MB><<<grid, 256, 0, s>>>(
+              items, sc->n_etasks, ptr, col, val, B, (int)ldb, C, (int)ldc, nchunk, ep);
+        else if (ep.mode == 1)
+          k_spmm_warp<V, TIn, false, 1, U, MB><<<grid, 256, 0, s>>>(
+              items, sc->n_etasks, ptr, col, val, B, (int)ldb, C, (int)ldc, nchunk, ep);
+        else
+          k_spmm_warp<V, TIn, false, 2, U, MB><<<grid, 256, 0, s>>>(
+              items, sc->n_etasks, ptr, col, val, B, (int)ldb, C, (int)ldc, nchunk, ep);
+        ::abg::note_launch();
+      }
+      tma = true;
     }
   }
   if (tma) {
