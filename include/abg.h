@@ -131,6 +131,10 @@ ABG_API void abg_params_default(abg_params* p);   /* k=2, gamma=6, alpha=.6, t_f
 /* Number of CUDA kernels this library has launched in the calling process so
  * far (a diagnostic counter; every launch site increments it). */
 ABG_API int64_t abg_launch_count(void);
+/* Of those, the launches of the tensor-core (tcgen05) product kernel. Dense
+ * tall-skinny products run there unless the environment variable
+ * ABG_TENSOR_CORES is set to 0 (then on the FP32 SIMT kernels). */
+ABG_API int64_t abg_tensor_core_launches(void);
 
 /* ---- graph lifetime ------------------------------------------------------ */
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "abg_last_error": (C.c_char_p, []),
     "abg_params_default": (None, [_p]),
     "abg_launch_count": (_i64, []),
+    "abg_tensor_core_launches": (_i64, []),
     "abg_create": (C.c_int, [_p, _p, _p]),
     "abg_destroy": (None, [_p]),
     "abg_graph_footprint": (_i64, [_p]),
@@ -235,6 +236,10 @@ def abg_cluster(graph: Graph, p: abg_params, labels=None, stream=None):
 
 def abg_launch_count() -> int:
     return int(lib().abg_launch_count())
+
+
+def abg_tensor_core_launches() -> int:
+    return int(lib().abg_tensor_core_launches())
 
 
 def _desc_of(g, keep: list) -> abg_graph_desc:

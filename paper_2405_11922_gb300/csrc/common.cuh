@@ -46,6 +46,7 @@ int cuda_status(cudaError_t e, const char* what);
 
 // kernel launches issued by this library in this process (diagnostic counter)
 void note_launch();
+void note_tc_launch();  // a tensor-core kernel launch (also counted by note_launch)
 
 // ---------------------------------------------------------------------------
 // stream-ordered device memory from a private pool per device

@@ -264,6 +264,9 @@ int gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s) {
   ABG_CHECK(a.lda % 4 == 0 && a.ldb % 4 == 0 && a.lda >= a.K && a.ldb >= a.N,
             "gemm_nn: leading dimensions must be multiples of 4 and cover the width");
   if (rs.n_tiles == 0) return ABG_OK;
+  bool tc = false;
+  ABG_TRY(tc_gemm_nn(rs, a, s, &tc));
+  if (tc) return ABG_OK;
   NNK p{a.A, a.lda, a.B, a.ldb, a.b_seg, a.C, a.ldc, a.N, a.K, a.segN, a.segK,
         rs.tile_seg, rs.tile_row0, rs.tile_rows, (int)a.epi, a.aux, a.ldaux, a.aux2, a.ldaux2,
         a.sign, a.sign_seg, a.in_scale, a.out_scale, a.colsum_part, a.labels, a.margin, a.first,

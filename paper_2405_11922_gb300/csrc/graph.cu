@@ -13,13 +13,16 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace abg {
 
 static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 
+static std::atomic<long long> g_tc_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_tc_launch() { g_tc_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -73,6 +76,22 @@ int raise_smem_limit(const void* func, size_t bytes) {
   ABG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   cur = bytes;
   return ABG_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
 }
 
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
@@ -495,6 +514,7 @@ ABG_API const char* abg_strerror(int st) {
 ABG_API const char* abg_last_error(void) { return g_err; }
 
 ABG_API int64_t abg_launch_count(void) { return g_launches.load(); }
+ABG_API int64_t abg_tensor_core_launches(void) { return g_tc_launches.load(); }
 
 ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out) {
   if (!out) {

@@ -12,11 +12,8 @@
 // edges are split into kHeavyChunk-edge chunks whose partial sums go to a
 // scratch buffer and are added back in chunk order, so results do not depend
 // on scheduling (no floating-point atomics).
-#include <cudaTypedefs.h>
-
-#include <mutex>
-
 #include "internal.cuh"
+#include "tma.cuh"
 
 namespace abg {
 
@@ -434,52 +431,6 @@ __global__ void __launch_bounds__(256, MINB)
 #endif
 constexpr int kTmaWarps = ABG_TMA_WARPS;     // warps (independent pipelines) per CTA
 constexpr int kTmaRingBytes = ABG_TMA_RING;  // gather ring per warp
-constexpr uint64_t kTmaWaitNs = 1000000000ull;  // a wait longer than 1 s counts as failed
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// bounded wait; false when it ran out
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kTmaWaitNs) return false;
-  return true;
-}
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int4 rows,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(rows.x), "r"(rows.y), "r"(rows.z),
-      "r"(rows.w), "r"(bar)
-      : "memory");
-}
-
 template <class TIn>
 __device__ __forceinline__ float4 smem_chunk(const unsigned char* row, int ch);
 template <>
@@ -797,22 +748,6 @@ static inline unsigned blocks_for(int64_t groups, int G) {
   return (unsigned)ceil_div(groups * G, 256);
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
 // Light tasks with edges through k_spmm_tma; *used stays false when the shape does not
 // fit its limits (row box of at most 256 elements, 16-byte rows and base).
 template <int V, class TIn>
@@ -1020,13 +955,16 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
 }
 
 int check_wait_flag(const abg_graph* g, cudaStream_t s) {
-  int flag = 0;
+  int flag = 0, tc = 0;
   ABG_CUDA(cudaMemcpyAsync(&flag, g->wait_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  ABG_CUDA(cudaStreamSynchronize(s));
-  if (flag == 0) return ABG_OK;
-  ABG_CUDA(cudaMemsetAsync(g->wait_err, 0, sizeof(int), s));
-  ABG_CUDA(cudaStreamSynchronize(s));
-  set_error("a bounded wait in the SpMM gather pipeline ran out; its results are invalid");
+  ABG_TRY(tc_wait_flag(s, &tc));  // synchronises s
+  if (flag == 0 && tc == 0) return ABG_OK;
+  if (flag) {
+    ABG_CUDA(cudaMemsetAsync(g->wait_err, 0, sizeof(int), s));
+    ABG_CUDA(cudaStreamSynchronize(s));
+  }
+  set_error("a bounded wait in the %s pipeline ran out; its results are invalid",
+            flag ? "SpMM gather" : "tensor-core GEMM");
   return ABG_EDEVICE;
 }
 

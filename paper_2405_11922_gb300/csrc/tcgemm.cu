@@ -1,0 +1,497 @@
+// Tall-skinny products C = A B_s on the 5th-generation tensor cores
+// (tcgen05.mma kind::tf32, accumulator in tensor memory).
+//
+// A (rows x K, fp32, row-major) is the tall operand, B_s (K x N per segment)
+// the small one. One CTA computes a 128-row tile (one UMMA M) for the tile's
+// segment, streaming K in 32-column blocks (one 128-byte swizzle row) through
+// a ring of shared-memory stages:
+//   warp 0      TMA producer: A block, B_hi and B_lo blocks (128B swizzle)
+//   warp 1      allocates tensor memory; one thread issues the MMAs
+//   warps 2..5  split the A block in place into tf32 hi and lo parts, then run
+//               the epilogue (tcgen05.ld of their 32-lane quarter of TMEM)
+// Three-term split (the usual 3xTF32 scheme): x = hi + lo with
+// hi = rna_tf32(x), lo = rna_tf32(x - hi), and A B ~ hi(A) hi(B) + lo(A) hi(B)
+// + hi(A) lo(B); both parts are exact tf32 values, so the operand precision is
+// about 2^-21 relative, with fp32 accumulation. B_hi / B_lo are prepared once
+// per call by a small kernel (transposed to K-major, zero outside K_s x N_s).
+// Every mbarrier wait is bounded; a wait that runs out sets a device flag
+// (read by tc_wait_flag) and the CTA still frees its tensor memory.
+#include <cstdlib>
+#include <cstring>
+
+#include "batch.cuh"
+#include "internal.cuh"
+#include "tma.cuh"
+
+namespace abg {
+
+namespace {
+
+constexpr int kTcM = 128;        // rows per tile = UMMA M
+constexpr int kTcBK = 32;        // K per stage (fp32: one 128-byte swizzle row)
+constexpr int kTcThreads = 192;  // 6 warps
+constexpr uint32_t kTcABytes = kTcM * kTcBK * 4;  // 16 KiB
+
+__device__ int g_tc_wait_err = 0;
+
+struct TcArgs {
+  int nkb;       // K blocks
+  int Np;        // UMMA N (multiple of 16, <= 256)
+  int N, K;      // largest N_s, K_s
+  const int* segN;
+  const int* segK;
+  const int* tile_seg;
+  const int64_t* tile_row0;
+  const int* tile_rows;
+  float* C;
+  int64_t ldc;
+  int epi;
+  const float* aux;
+  int64_t ldaux;
+  const float* aux2;
+  int64_t ldaux2;
+  const float* sign;
+  int64_t sign_seg;
+  int32_t* labels;
+  float* margin;
+  int first;
+  int* changes;
+  unsigned* minbits;
+  int stages;
+  uint32_t stage_bytes;
+  uint32_t b_bytes;
+  uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ float rna_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// B_hi / B_lo (segment s rows s*Np .. s*Np + Np, K-major, Kp columns) from B_s (K x N row-major)
+__global__ void k_tc_prep_b(const float* __restrict__ B, int64_t ldb, int64_t b_seg,
+                            const int* __restrict__ segK, int K, const int* __restrict__ segN, int N,
+                            int Np, int Kp, float* __restrict__ bhi, float* __restrict__ blo) {
+  const int sg = blockIdx.y;
+  const int Ks = segK ? segK[sg] : K;
+  const int Ns = segN ? segN[sg] : N;
+  const float* Bs = B + sg * b_seg;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Np * Kp;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / Kp), k = (int)(e % Kp);
+    float h = 0.f, l = 0.f;
+    if (n < Ns && k < Ks) {
+      const float x = Bs[(int64_t)k * ldb + n];
+      h = rna_tf32(x);
+      l = rna_tf32(x - h);
+    }
+    const int64_t o = ((int64_t)sg * Np + n) * Kp + k;
+    bhi[o] = h;
+    blo[o] = l;
+  }
+}
+
+struct Best {
+  float v;
+  int i;
+  float s;
+};
+__device__ __forceinline__ void push_best(Best& b, float v, int i) {
+  if (v > b.v) {  // columns arrive in increasing order: ties keep the lower index
+    b.s = b.v;
+    b.v = v;
+    b.i = i;
+  } else if (v > b.s) {
+    b.s = v;
+  }
+}
+
+template <bool ARGMAX>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_nn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bhi_map,
+            const __grid_constant__ CUtensorMap blo_map, const TcArgs p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x;
+  const int sg = p.tile_seg[tile];
+  const int64_t row0 = p.tile_row0[tile];
+  const int nrows = p.tile_rows[tile];
+  const int Ks = p.segK ? p.segK[sg] : p.K;
+  const int Ns = p.segN ? p.segN[sg] : p.N;
+  const int S = p.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
+  const uint32_t full0 = smem_addr(bars), split0 = full0 + 8 * S, empty0 = full0 + 16 * S,
+                 accb = full0 + 24 * S;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(split0 + 8 * i, 128);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  // after a wait has run out anywhere, later CTAs skip their work instead of waiting again
+  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int s = 0;
+      uint32_t ph = 0;
+      for (int kb = 0; kb < p.nkb && !bad; ++kb) {
+        if (kb >= S && !mbar_wait_bounded(empty0 + 8 * s, ph ^ 1u)) {
+          bad = true;
+          break;
+        }
+        const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
+        mbar_expect_tx(full0 + 8 * s, kTcABytes + 2 * p.b_bytes);
+        tma_load_2d(st, &amap, kb * kTcBK, (int)row0, full0 + 8 * s);
+        tma_load_2d(st + 2 * kTcABytes, &bhi_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
+        tma_load_2d(st + 2 * kTcABytes + p.b_bytes, &blo_map, kb * kTcBK, sg * p.Np,
+                    full0 + 8 * s);
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = tf32_idesc(p.Np);
+      int s = 0;
+      uint32_t ph = 0;
+      for (int kb = 0; kb < p.nkb && !bad; ++kb) {
+        if (!mbar_wait_bounded(full0 + 8 * s, ph) || !mbar_wait_bounded(split0 + 8 * s, ph)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
+        const uint32_t a_hi = st, a_lo = st + kTcABytes, b_hi = st + 2 * kTcABytes,
+                       b_lo = b_hi + p.b_bytes;
+#pragma unroll
+        for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 32 bytes
+          const uint32_t off = 32u * j;
+          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
+                   (kb | j) != 0);
+          mma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+        }
+        mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!bad) mma_commit(accb);
+    }
+  } else {
+    // split the A block into tf32 hi (in place) and lo parts; zero columns >= K_s
+    const int t = threadIdx.x - 64;
+    int s = 0;
+    uint32_t ph = 0;
+    for (int kb = 0; kb < p.nkb && !bad; ++kb) {
+      if (!mbar_wait_bounded(full0 + 8 * s, ph)) {
+        bad = true;
+        break;
+      }
+      float4* a = reinterpret_cast<float4*>(smem + (size_t)s * p.stage_bytes);
+      float4* alo = a + kTcABytes / 16;
+#pragma unroll 4
+      for (int q = t; q < (int)(kTcABytes / 16); q += 128) {
+        const int r = q >> 3;
+        const int lc = (q & 7) ^ (r & 7);  // logical 16-byte chunk under the 128-byte swizzle
+        const int k0 = kb * kTcBK + lc * 4;
+        const float4 v = a[q];
+        float4 h, l;
+        h.x = k0 < Ks ? rna_tf32(v.x) : 0.f;
+        h.y = k0 + 1 < Ks ? rna_tf32(v.y) : 0.f;
+        h.z = k0 + 2 < Ks ? rna_tf32(v.z) : 0.f;
+        h.w = k0 + 3 < Ks ? rna_tf32(v.w) : 0.f;
+        l.x = k0 < Ks ? rna_tf32(v.x - h.x) : 0.f;
+        l.y = k0 + 1 < Ks ? rna_tf32(v.y - h.y) : 0.f;
+        l.z = k0 + 2 < Ks ? rna_tf32(v.z - h.z) : 0.f;
+        l.w = k0 + 3 < Ks ? rna_tf32(v.w - h.w) : 0.f;
+        a[q] = h;
+        alo[q] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+      mbar_arrive(split0 + 8 * s);
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    // epilogue: this warp's quarter of the accumulator lanes = rows
+    bad = __any_sync(0xffffffffu, bad) || !mbar_wait_bounded(accb, 0);
+    bad = __any_sync(0xffffffffu, bad);
+    if (!bad) {
+      tc_fence_after();
+      const int quad = warp & 3;
+      const int r = quad * 32 + lane;
+      const int64_t gm = row0 + r;
+      const bool valid = r < nrows;
+      Best b{-INFINITY, 0x7fffffff, -INFINITY};
+      for (int c0 = 0; c0 < p.Np; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+        if (!valid) continue;
+        if constexpr (ARGMAX) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < Ns) push_best(b, v[j], c0 + j);
+        } else {
+          float* crow = p.C + gm * p.ldc;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int gn = c0 + j;
+            float x = v[j];
+            if (gn < Ns) {
+              switch (p.epi) {
+                case (int)Epi::Relu: x = fmaxf(x, 0.f); break;
+                case (int)Epi::SignRelu: x = fmaxf(p.sign[sg * p.sign_seg + gn] * x, 0.f); break;
+                case (int)Epi::Sign: x = p.sign[sg * p.sign_seg + gn] * x; break;
+                case (int)Epi::PhiUpdate: {
+                  const float pv = p.aux[gm * p.ldaux + gn];
+                  const float phi = p.aux2[gm * p.ldaux2 + gn];
+                  x = x > 0.f ? phi * sqrtf(fmaxf(pv, 0.f) / x) : 0.f;
+                  break;
+                }
+                default: break;
+              }
+            }
+            v[j] = x;
+          }
+          // 16-byte stores where four columns are in range (ldc is a multiple of 4)
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            const int gn = c0 + j;
+            if (gn + 3 < Ns) {
+              *reinterpret_cast<float4*>(crow + gn) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (gn + q < Ns) crow[gn + q] = v[j + q];
+            }
+          }
+        }
+      }
+      if constexpr (ARGMAX) {
+        int changed = 0;
+        float mg = INFINITY;
+        if (valid) {
+          mg = Ns > 1 ? b.v - b.s : INFINITY;
+          if (!p.first && p.labels[gm] != b.i) changed = 1;
+          p.labels[gm] = b.i;
+          if (p.margin) p.margin[gm] = mg;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          changed += __shfl_xor_sync(0xffffffffu, changed, o);
+          mg = fminf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+        }
+        if (lane == 0) {
+          if (changed) atomicAdd(p.changes + sg, changed);
+          if (mg < INFINITY) atomicMin(p.minbits + sg, __float_as_uint(fmaxf(mg, 0.f)));
+        }
+      }
+    }
+  }
+  if (bad) atomicExch(&g_tc_wait_err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+bool tc_disabled() {
+  const char* e = std::getenv("ABG_TENSOR_CORES");
+  return e && e[0] == '0';
+}
+
+}  // namespace
+
+int tc_wait_flag(cudaStream_t s, int* flag) {
+  *flag = 0;
+  ABG_CUDA(cudaMemcpyFromSymbolAsync(flag, g_tc_wait_err, sizeof(int), 0,
+                                     cudaMemcpyDeviceToHost, s));
+  ABG_CUDA(cudaStreamSynchronize(s));
+  if (*flag) {
+    const int zero = 0;
+    ABG_CUDA(cudaMemcpyToSymbolAsync(g_tc_wait_err, &zero, sizeof(int), 0,
+                                     cudaMemcpyHostToDevice, s));
+    ABG_CUDA(cudaStreamSynchronize(s));
+  }
+  return ABG_OK;
+}
+
+int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
+  static_assert(kTile == kTcM, "row-space tiles must match the UMMA M");
+  *used = false;
+  if (a.ldc % 4 != 0 || reinterpret_cast<uintptr_t>(a.C) % 16 != 0) return ABG_OK;
+  if (tc_disabled() || a.sincos || a.N > 256 || rs.n_tiles == 0) return ABG_OK;
+  if (a.lda % 4 != 0 || reinterpret_cast<uintptr_t>(a.A) % 16 != 0 || rs.rows > INT32_MAX)
+    return ABG_OK;
+  const auto enc = tensor_map_encoder();
+  if (!enc) return ABG_OK;
+  const int nseg = rs.nseg;
+  const int Np = (int)round_up(a.N, 16);
+  const int nkb = (int)ceil_div(a.K, kTcBK);
+  const int Kp = nkb * kTcBK;
+  if ((int64_t)nseg * Np > INT32_MAX) return ABG_OK;
+  Scratch scr(s);
+  float *bhi, *blo;
+  ABG_TRY(scr.get(&bhi, (size_t)nseg * Np * Kp));
+  ABG_TRY(scr.get(&blo, (size_t)nseg * Np * Kp));
+  {
+    const int64_t work = (int64_t)Np * Kp;
+    dim3 g((unsigned)std::min<int64_t>(ceil_div(work, 256), 256), (unsigned)nseg);
+    k_tc_prep_b<<<g, 256, 0, s>>>(a.B, a.ldb, a.b_seg, a.segK, a.K, a.segN, a.N, Np, Kp, bhi, blo);
+    note_launch();
+    ABG_LAUNCH_CHECK();
+  }
+  CUtensorMap amap, hmap, lmap;
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.lda * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcM};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.A), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)nseg * Np};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)Np};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&hmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bhi, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&lmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, blo, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  TcArgs p{};
+  p.nkb = nkb;
+  p.Np = Np;
+  p.N = a.N;
+  p.K = a.K;
+  p.segN = a.segN;
+  p.segK = a.segK;
+  p.tile_seg = rs.tile_seg;
+  p.tile_row0 = rs.tile_row0;
+  p.tile_rows = rs.tile_rows;
+  p.C = a.C;
+  p.ldc = a.ldc;
+  p.epi = (int)a.epi;
+  p.aux = a.aux;
+  p.ldaux = a.ldaux;
+  p.aux2 = a.aux2;
+  p.ldaux2 = a.ldaux2;
+  p.sign = a.sign;
+  p.sign_seg = a.sign_seg;
+  p.labels = a.labels;
+  p.margin = a.margin;
+  p.first = a.first;
+  p.changes = a.changes;
+  p.minbits = a.minbits;
+  p.b_bytes = (uint32_t)Np * kTcBK * 4;
+  p.stage_bytes = 2 * kTcABytes + 2 * p.b_bytes;  // multiple of 1024
+  p.stages = (int)std::max<int64_t>(2, std::min<int64_t>(4, (200 * 1024) / p.stage_bytes));
+  p.tmem_cols = 32;
+  while ((int)p.tmem_cols < Np) p.tmem_cols *= 2;
+  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 8 * (3 * p.stages + 1);
+  if (smem > 227 * 1024) return ABG_OK;
+  const void* fn = a.argmax ? (const void*)k_tc_nn<true> : (const void*)k_tc_nn<false>;
+  ABG_TRY(raise_smem_limit(fn, smem));
+  if (a.argmax)
+    k_tc_nn<true><<<(unsigned)rs.n_tiles, kTcThreads, smem, s>>>(amap, hmap, lmap, p);
+  else
+    k_tc_nn<false><<<(unsigned)rs.n_tiles, kTcThreads, smem, s>>>(amap, hmap, lmap, p);
+  note_launch();
+  note_tc_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
+}  // namespace abg
