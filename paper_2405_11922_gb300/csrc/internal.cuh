@@ -62,6 +62,7 @@ struct abg_graph {
 namespace abg {
 
 constexpr int kMaxK = 128;     // clusters supported by the NCI kernels
+constexpr int kMaxRsvdBlock = 1024;  // randomized-SVD block width (and orthogonal-matrix size)
 constexpr int kMaxD = 1024;    // feature width supported by the SpMMs
 #ifndef ABG_TASK_EDGES
 #define ABG_TASK_EDGES 128

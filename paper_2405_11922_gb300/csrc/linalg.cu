@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl,
   const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
   __shared__ double s_piv;
   __shared__ double s_maxdiag;
+  __shared__ double s_rinv[kMaxRsvdBlock];
   for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
     const int i = (int)(q / l), j = (int)(q % l);
     R[q] = j >= i ? G[(int64_t)i * ldg + j] : 0.0;
@@ -142,21 +143,25 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl,
   }
   __syncthreads();
   const double tol = 1e-13 * s_maxdiag;
+  // FP64 divisions and square roots are slow: one of each per pivot, multiplications elsewhere
+  double* rinv = s_rinv;
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
       const double p = R[(int64_t)j * l + j];
       if (!(p > tol)) {
         s_piv = 0.0;
+        rinv[j] = 0.0;
         atomicAdd(breakdowns, 1);
       } else {
         s_piv = sqrt(p);
+        rinv[j] = 1.0 / s_piv;
       }
     }
     __syncthreads();
-    const double piv = s_piv;
+    const double piv = s_piv, ip = rinv[j];
     for (int c = j + tid; c < l; c += nt) {
       const double v = R[(int64_t)j * l + c];
-      R[(int64_t)j * l + c] = piv > 0.0 ? (c == j ? piv : v / piv) : 0.0;
+      R[(int64_t)j * l + c] = piv > 0.0 ? (c == j ? piv : v * ip) : 0.0;
     }
     __syncthreads();
     for (int r = j + 1 + warp; r < l; r += nw) {
@@ -165,23 +170,24 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl,
     }
     __syncthreads();
   }
-  for (int j = warp; j < l; j += nw) {
-    for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
-    __syncwarp();
-    for (int i = j; i >= 0; --i) {
-      const double rii = R[(int64_t)i * l + i];
-      double acc = 0.0;
-      for (int p = i + 1 + lane; p <= j; p += 32) acc += R[(int64_t)i * l + p] * Ri[(int64_t)p * l + j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
-        const double rhs = (i == j ? 1.0 : 0.0) - acc;
-        Ri[(int64_t)i * l + j] = rii > 0.0 ? rhs / rii : 0.0;
+  // Ri = R^-1 (upper triangular), one row at a time from the bottom:
+  // Ri[i][j] = -(1/R[i][i]) sum_{i<p<=j} R[i][p] Ri[p][j], Ri[i][i] = 1/R[i][i]
+  for (int64_t q = tid; q < (int64_t)l * l; q += nt) Ri[q] = 0.0;
+  __syncthreads();
+  for (int i = l - 1; i >= 0; --i) {
+    const double ii = rinv[i];
+    for (int j = i + tid; j < l; j += nt) {
+      double v;
+      if (j == i) {
+        v = ii;
+      } else {
+        double acc = 0.0;
+        for (int p = i + 1; p <= j; ++p) acc += R[(int64_t)i * l + p] * Ri[(int64_t)p * l + j];
+        v = -ii * acc;
       }
-      __syncwarp();
+      Ri[(int64_t)i * l + j] = v;
     }
-    if (R[(int64_t)j * l + j] <= 0.0)
-      for (int i = lane; i < l; i += 32) Ri[(int64_t)i * l + j] = 0.0;
+    __syncthreads();
   }
   __syncthreads();
   for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
@@ -387,143 +393,131 @@ int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy
 }
 
 // ---------------------------------------------------------------------------
-// Parallel cyclic Jacobi, one CTA per segment, for the symmetric l_s x l_s FP64
-// matrix A_s (row stride lmax inside a lmax^2 slab; round-robin pairing so the
-// l/2 rotations of a step touch disjoint index pairs). A_s is destroyed;
-// evals_s (descending) and evecs_s (columns, row stride lmax) are written.
+// One-sided (Hestenes) Jacobi SVD in FP32, one CTA per segment: the columns of
+// W_s = Bt_s (m x l_s, FP64 input, row stride lmax inside an m*lmax slab) are
+// rotated in round-robin order (the l/2 rotations of a step touch disjoint
+// column pairs, one warp per pair) until every pair is orthogonal to ~1e-6 of
+// its norms; then sigma_j = |w_j| and V holds the accumulated rotations, the
+// right singular vectors of Bt_s = the eigenvectors of Bt_s^T Bt_s. FP32 keeps
+// the error of sigma_j near 1e-7 sigma_1, the accuracy of the FP32 products
+// that formed Bt_s, at a fraction of the cost of FP64 on this GPU.
+// evals_s (sigma^2, descending) and evecs_s (columns, row stride lmax) are written.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_jacobi(const int* __restrict__ segl, int lmax,
-                                                 double* __restrict__ Aall, double* __restrict__ Vall,
-                                                 double* __restrict__ evals,
-                                                 double* __restrict__ evecs, int max_sweeps,
-                                                 int a_smem, int v_smem) {
-  extern __shared__ double js[];
+__global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restrict__ segl,
+                                                       int lmax, const double* __restrict__ Btall,
+                                                       float* __restrict__ Wg_all,
+                                                       float* __restrict__ Vg_all, int in_smem,
+                                                       int max_sweeps, double* __restrict__ evals,
+                                                       double* __restrict__ evecs) {
+  extern __shared__ float sv_smem[];
+  __shared__ int s_rot;
   const int sg = blockIdx.x;
   const int l = segl[sg];
-  const int64_t l2 = (int64_t)lmax * lmax;
-  double* Ag = Aall + sg * l2;
-  double* Vg = Vall + sg * l2;
+  const double* Bt = Btall + (int64_t)sg * m * lmax;
+  // column-major: column j of W at W + j*m, of V at V + j*l
+  float* W = in_smem ? sv_smem : Wg_all + (int64_t)sg * m * lmax;
+  float* V = in_smem ? sv_smem + (int64_t)m * l : Vg_all + (int64_t)sg * lmax * lmax;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int m = (l + 1) & ~1;  // even player count (index l is a dummy when l is odd)
-  const int P = m / 2;
-  const int Pmax = ((lmax + 1) & ~1) / 2;
-  double* cs = js;
-  double* sn = js + Pmax;
-  int* pp = reinterpret_cast<int*>(js + 2 * Pmax);
-  int* qq = pp + Pmax;
-  double* red = js + 3 * Pmax + 1;          // 2 * nt + 1
-  double* tail = red + 2 * nt + 2;
-  // matrices use row stride l inside shared memory, lmax in global memory
-  const int lda = a_smem ? l : lmax;
-  const int ldv = v_smem ? l : lmax;
-  double* A = a_smem ? tail : Ag;
-  double* V = v_smem ? tail + (a_smem ? l2 : 0) : Vg;
-  if (a_smem)
-    for (int64_t q = tid; q < (int64_t)l * l; q += nt) A[q] = Ag[(q / l) * lmax + q % l];
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt)
-    V[(q / l) * ldv + q % l] = ((q / l) == (q % l)) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
-      const double v = A[(q / l) * lda + q % l];
-      tot += v * v;
-      if ((q / l) != (q % l)) off += v * v;
-    }
-    red[tid] = off;
-    red[nt + tid] = tot;
-    __syncthreads();
-    if (tid == 0) {
-      double o = 0.0, t = 0.0;
-      for (int i = 0; i < nt; ++i) {
-        o += red[i];
-        t += red[nt + i];
-      }
-      red[2 * nt] = (o <= 1e-30 * t || t == 0.0) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (red[2 * nt] != 0.0) break;
-    __syncthreads();
-    for (int step = 0; step < m - 1; ++step) {
-      for (int i = tid; i < P; i += nt) {
-        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (m - 1)) + 1; };
-        int a = player(i), b = player(m - 1 - i);
-        int p = min(a, b), q = max(a, b);
-        double c = 1.0, sv = 0.0;
-        if (q < l) {
-          const double apq = A[(int64_t)p * lda + q];
-          if (apq != 0.0) {
-            const double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            sv = t * c;
-          }
-        }
-        cs[i] = c;
-        sn[i] = sv;
-        pp[i] = p;
-        qq[i] = q;
-      }
-      __syncthreads();
-      const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-      for (int i = warp; i < P; i += nw) {  // rows: A <- J^T A
-        const int p = pp[i], q = qq[i];
-        if (q >= l) continue;
-        const double c = cs[i], sv = sn[i];
-        for (int k = lane; k < l; k += 32) {
-          const double apk = A[(int64_t)p * lda + k], aqk = A[(int64_t)q * lda + k];
-          A[(int64_t)p * lda + k] = c * apk - sv * aqk;
-          A[(int64_t)q * lda + k] = sv * apk + c * aqk;
-        }
-      }
-      __syncthreads();
-      for (int i = warp; i < P; i += nw) {  // columns: A <- A J, V <- V J
-        const int p = pp[i], q = qq[i];
-        if (q >= l) continue;
-        const double c = cs[i], sv = sn[i];
-        for (int k = lane; k < l; k += 32) {
-          const double akp = A[(int64_t)k * lda + p], akq = A[(int64_t)k * lda + q];
-          A[(int64_t)k * lda + p] = c * akp - sv * akq;
-          A[(int64_t)k * lda + q] = sv * akp + c * akq;
-          const double vkp = V[(int64_t)k * ldv + p], vkq = V[(int64_t)k * ldv + q];
-          V[(int64_t)k * ldv + p] = c * vkp - sv * vkq;
-          V[(int64_t)k * ldv + q] = sv * vkp + c * vkq;
-        }
-      }
-      __syncthreads();
-    }
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int64_t q = tid; q < (int64_t)m * l; q += nt) {
+    const int j = (int)(q / m), r = (int)(q % m);
+    W[q] = (float)Bt[(int64_t)r * lmax + j];
   }
-  // sort descending (rank by value, ties by index) and write eigenpairs
+  for (int64_t q = tid; q < (int64_t)l * l; q += nt) V[q] = (q / l) == (q % l) ? 1.f : 0.f;
+  __syncthreads();
+  const int mp = (l + 1) & ~1;  // even player count; index l is a bye when l is odd
+  const int P = mp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int step = 0; step < mp - 1; ++step) {
+      for (int i = warp; i < P; i += nw) {
+        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (mp - 1)) + 1; };
+        const int a = player(i), b = player(mp - 1 - i);
+        const int pc = min(a, b), qc = max(a, b);
+        if (qc >= l) continue;
+        float* wp = W + (int64_t)pc * m;
+        float* wq = W + (int64_t)qc * m;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int r = lane; r < m; r += 32) {
+          const float x = wp[r], y = wq[r];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (!(fabsf(ga) > 1e-6f * sqrtf(al * be))) continue;  // uniform over the warp
+        const float zeta = (be - al) / (2.f * ga);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        const float c = rsqrtf(fmaf(t, t, 1.f));
+        const float sn = c * t;
+        for (int r = lane; r < m; r += 32) {
+          const float x = wp[r], y = wq[r];
+          wp[r] = c * x - sn * y;
+          wq[r] = sn * x + c * y;
+        }
+        float* vp = V + (int64_t)pc * l;
+        float* vq = V + (int64_t)qc * l;
+        for (int r = lane; r < l; r += 32) {
+          const float x = vp[r], y = vq[r];
+          vp[r] = c * x - sn * y;
+          vq[r] = sn * x + c * y;
+        }
+        rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (rotated && lane == 0) atomicOr(&s_rot, 1);
+    __syncthreads();
+    if (s_rot == 0) break;
+  }
+  // sigma_j^2 = |w_j|^2 (one warp per column), then rank descending (ties by index)
+  __syncthreads();
+  __shared__ float s_norm[kMaxRsvdBlock];
+  for (int j = warp; j < l; j += nw) {
+    const float* wj = W + (int64_t)j * m;
+    float acc = 0.f;
+    for (int r = lane; r < m; r += 32) acc = fmaf(wj[r], wj[r], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s_norm[j] = acc;
+  }
+  __syncthreads();
   double* ev = evals + (int64_t)sg * lmax;
-  double* ec = evecs + sg * l2;
+  double* ec = evecs + (int64_t)sg * lmax * lmax;
   for (int i = tid; i < l; i += nt) {
-    const double li = A[(int64_t)i * lda + i];
+    const float li = s_norm[i];
     int rank = 0;
     for (int j = 0; j < l; ++j) {
-      const double lj = A[(int64_t)j * lda + j];
+      const float lj = s_norm[j];
       rank += (lj > li) || (lj == li && j < i);
     }
-    ev[rank] = li;
-    for (int k = 0; k < l; ++k) ec[(int64_t)k * lmax + rank] = V[(int64_t)k * ldv + i];
+    ev[rank] = (double)li;
+    for (int k = 0; k < l; ++k) ec[(int64_t)k * lmax + rank] = (double)V[(int64_t)i * l + k];
   }
 }
 
-static int jacobi_eig(int nseg, const int* segl, int lmax, double* A, double* evals, double* evecs,
-                      cudaStream_t s) {
+static int svd_onesided(int nseg, int m, const int* segl, int lmax, const double* Bt,
+                        double* evals, double* evecs, cudaStream_t s) {
+  ABG_CHECK(lmax <= kMaxRsvdBlock, "svd: block width above %d", kMaxRsvdBlock);
   Scratch scr(s);
-  double* V;
-  ABG_TRY(scr.get(&V, (size_t)nseg * lmax * lmax));
-  const int threads = 1024;
-  const int P = ((lmax + 1) & ~1) / 2;
-  const size_t base = sizeof(double) * (3 * P + 1 + 2 * threads + 2);
-  const size_t mat = sizeof(double) * (size_t)lmax * lmax;
-  const size_t limit = 220 * 1024;
-  const int a_smem = base + mat <= limit;
-  const int v_smem = a_smem && base + 2 * mat <= limit;
-  const size_t smem = base + (a_smem ? mat : 0) + (v_smem ? mat : 0);
-  ABG_TRY(raise_smem_limit((const void*)k_jacobi, smem));
-  k_jacobi<<<(unsigned)nseg, threads, smem, s>>>(segl, lmax, A, V, evals, evecs, 40, a_smem, v_smem);
+  const size_t smem = sizeof(float) * ((size_t)m * lmax + (size_t)lmax * lmax);
+  const int in_smem = smem <= 200 * 1024;
+  float *W = nullptr, *V = nullptr;
+  if (!in_smem) {
+    ABG_TRY(scr.get(&W, (size_t)nseg * m * lmax));
+    ABG_TRY(scr.get(&V, (size_t)nseg * lmax * lmax));
+  } else {
+    ABG_TRY(raise_smem_limit((const void*)k_svd_onesided, smem));
+  }
+  k_svd_onesided<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(m, segl, lmax, Bt, W, V, in_smem,
+                                                                   40, evals, evecs);
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
@@ -634,14 +628,13 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   const int64_t kk = round_up(kmax, 4);
   const int64_t l2 = (int64_t)lmax * lmax;
   float *Om, *Y, *T1, *Yt, *T2, *Bm;
-  double *Bt, *M, *evals, *evecs, *qsum, *Uks, *Hd;
+  double *Bt, *evals, *evecs, *qsum, *Uks, *Hd;
   ABG_TRY(scr.get(&Om, (size_t)nseg * m * ll));
   ABG_TRY(scr.get(&Y, (size_t)rs.rows * ll));
   ABG_TRY(scr.get(&T1, (size_t)rs.rows * ll));
   ABG_TRY(scr.get(&Yt, (size_t)nseg * m * ll));
   ABG_TRY(scr.get(&T2, (size_t)nseg * m * ll));
   ABG_TRY(scr.get(&Bt, (size_t)nseg * m * lmax));
-  ABG_TRY(scr.get(&M, (size_t)nseg * l2));
   ABG_TRY(scr.get(&evals, (size_t)nseg * lmax));
   ABG_TRY(scr.get(&evecs, (size_t)nseg * l2));
   ABG_TRY(scr.get(&qsum, (size_t)nseg * lmax));
@@ -677,16 +670,9 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
     }
   }
   Y = cur;
-  // B^T = A^T Q (m x l), B B^T = Bt^T Bt (l x l), eigenpairs
+  // B^T = A^T Q (m x l); its SVD gives sigma and the left singular vectors of B
   ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
-  {
-    dim3 g((unsigned)ceil_div(l2, 128), (unsigned)nseg);
-    k_small_tn64<<<g, 128, 0, s>>>(m, ss.l, lmax, ss.l, lmax, Bt, lmax, (int64_t)m * lmax, Bt, lmax,
-                                   (int64_t)m * lmax, M, lmax, l2);
-    note_launch();
-  }
-  ABG_LAUNCH_CHECK();
-  ABG_TRY(jacobi_eig(nseg, ss.l, lmax, M, evals, evecs, s));
+  ABG_TRY(svd_onesided(nseg, m, ss.l, lmax, Bt, evals, evecs, s));
   ABG_TRY(column_sums(rs, lmax, Y, ll, qsum, lmax, s));
   {
     dim3 g((unsigned)ceil_div(kmax, 128), (unsigned)nseg);
