@@ -7,8 +7,10 @@
 // a ring of shared-memory stages:
 //   warp 0      TMA producer: A block, B_hi and B_lo blocks (128B swizzle)
 //   warp 1      allocates tensor memory; one thread issues the MMAs
-//   warps 2..5  split the A block in place into tf32 hi and lo parts, then run
-//               the epilogue (tcgen05.ld of their 32-lane quarter of TMEM)
+//   warps 2..5  split the A block in place into tf32 hi and lo parts
+//   warps 6..9  epilogue (tcgen05.ld of their 32-lane quarter of TMEM)
+// The kernel is persistent (one CTA per SM walks its tiles) with two TMEM
+// accumulators, so a tile's MMAs overlap the previous tile's epilogue.
 // Three-term split (the usual 3xTF32 scheme): x = hi + lo with
 // hi = rna_tf32(x), lo = rna_tf32(x - hi), and A B ~ hi(A) hi(B) + lo(A) hi(B)
 // + hi(A) lo(B); both parts are exact tf32 values, so the operand precision is
@@ -29,7 +31,7 @@ namespace {
 
 constexpr int kTcM = 128;        // rows per tile = UMMA M
 constexpr int kTcBK = 32;        // K per stage (fp32: one 128-byte swizzle row)
-constexpr int kTcThreads = 192;  // 6 warps
+constexpr int kTcThreads = 320;  // 10 warps
 constexpr uint32_t kTcABytes = kTcM * kTcBK * 4;  // 16 KiB
 
 __device__ int g_tc_wait_err = 0;
@@ -164,32 +166,107 @@ __device__ __forceinline__ void push_best(Best& b, float v, int i) {
   }
 }
 
+// per-tile epilogue of one accumulator row (this thread's TMEM lane)
+template <bool ARGMAX>
+__device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, int quad, int lane,
+                                                int sg, int64_t row0, int nrows, int Ns) {
+  const int r = quad * 32 + lane;
+  const int64_t gm = row0 + r;
+  const bool valid = r < nrows;
+  Best b{-INFINITY, 0x7fffffff, -INFINITY};
+  for (int c0 = 0; c0 < p.Np; c0 += 32) {
+    float v[32];
+    tmem_ld32(tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+    if (!valid) continue;
+    if constexpr (ARGMAX) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < Ns) push_best(b, v[j], c0 + j);
+    } else {
+      float* crow = p.C + gm * p.ldc;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int gn = c0 + j;
+        float x = v[j];
+        if (gn < Ns) {
+          switch (p.epi) {
+            case (int)Epi::Relu: x = fmaxf(x, 0.f); break;
+            case (int)Epi::SignRelu: x = fmaxf(p.sign[sg * p.sign_seg + gn] * x, 0.f); break;
+            case (int)Epi::Sign: x = p.sign[sg * p.sign_seg + gn] * x; break;
+            case (int)Epi::PhiUpdate: {
+              const float pv = p.aux[gm * p.ldaux + gn];
+              const float phi = p.aux2[gm * p.ldaux2 + gn];
+              x = x > 0.f ? phi * sqrtf(fmaxf(pv, 0.f) / x) : 0.f;
+              break;
+            }
+            default: break;
+          }
+        }
+        v[j] = x;
+      }
+      // 16-byte stores where four columns are in range (ldc is a multiple of 4)
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        const int gn = c0 + j;
+        if (gn + 3 < Ns) {
+          *reinterpret_cast<float4*>(crow + gn) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (gn + q < Ns) crow[gn + q] = v[j + q];
+        }
+      }
+    }
+  }
+  if constexpr (ARGMAX) {
+    int changed = 0;
+    float mg = INFINITY;
+    if (valid) {
+      mg = Ns > 1 ? b.v - b.s : INFINITY;
+      if (!p.first && p.labels[gm] != b.i) changed = 1;
+      p.labels[gm] = b.i;
+      if (p.margin) p.margin[gm] = mg;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      changed += __shfl_xor_sync(0xffffffffu, changed, o);
+      mg = fminf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    }
+    if (lane == 0) {
+      if (changed) atomicAdd(p.changes + sg, changed);
+      if (mg < INFINITY) atomicMin(p.minbits + sg, __float_as_uint(fmaxf(mg, 0.f)));
+    }
+  }
+}
+
+// Persistent: CTA c takes tiles c, c + gridDim.x, ...; the stage ring runs across tile
+// boundaries and the accumulator alternates between two TMEM buffers, so the MMAs of a
+// tile overlap the epilogue of the previous one.
+//   warp 0: TMA producer      warp 1: TMEM owner + MMA issuer
+//   warps 2-5: tf32 split     warps 6-9: epilogue (TMEM lane quarter = warp % 4)
 template <bool ARGMAX>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_nn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bhi_map,
-            const __grid_constant__ CUtensorMap blo_map, const TcArgs p) {
+            const __grid_constant__ CUtensorMap blo_map, const TcArgs p, int64_t n_tiles) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x;
-  const int sg = p.tile_seg[tile];
-  const int64_t row0 = p.tile_row0[tile];
-  const int nrows = p.tile_rows[tile];
-  const int Ks = p.segK ? p.segK[sg] : p.K;
-  const int Ns = p.segN ? p.segN[sg] : p.N;
   const int S = p.stages;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * p.stage_bytes);
   const uint32_t full0 = smem_addr(bars), split0 = full0 + 8 * S, empty0 = full0 + 16 * S,
-                 accb = full0 + 24 * S;
+                 tfull0 = full0 + 24 * S, tempty0 = tfull0 + 16;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(split0 + 8 * i, 128);
       mbar_init(empty0 + 8 * i, 1);
     }
-    mbar_init(accb, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -203,6 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  const uint32_t acc_cols = p.tmem_cols / 2;  // columns of one accumulator buffer
   // after a wait has run out anywhere, later CTAs skip their work instead of waiting again
   bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
 
@@ -210,20 +288,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {  // producer
       int s = 0;
       uint32_t ph = 0;
-      for (int kb = 0; kb < p.nkb && !bad; ++kb) {
-        if (kb >= S && !mbar_wait_bounded(empty0 + 8 * s, ph ^ 1u)) {
-          bad = true;
-          break;
-        }
-        const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
-        mbar_expect_tx(full0 + 8 * s, kTcABytes + 2 * p.b_bytes);
-        tma_load_2d(st, &amap, kb * kTcBK, (int)row0, full0 + 8 * s);
-        tma_load_2d(st + 2 * kTcABytes, &bhi_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
-        tma_load_2d(st + 2 * kTcABytes + p.b_bytes, &blo_map, kb * kTcBK, sg * p.Np,
-                    full0 + 8 * s);
-        if (++s == S) {
-          s = 0;
-          ph ^= 1u;
+      int64_t n = 0;  // stages issued so far
+      for (int64_t tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x) {
+        const int sg = p.tile_seg[tile];
+        const int row0 = (int)p.tile_row0[tile];
+        for (int kb = 0; kb < p.nkb; ++kb, ++n) {
+          if (n >= S && !mbar_wait_bounded(empty0 + 8 * s, ph ^ 1u)) {
+            bad = true;
+            break;
+          }
+          const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
+          mbar_expect_tx(full0 + 8 * s, kTcABytes + 2 * p.b_bytes);
+          tma_load_2d(st, &amap, kb * kTcBK, row0, full0 + 8 * s);
+          tma_load_2d(st + 2 * kTcABytes, &bhi_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
+          tma_load_2d(st + 2 * kTcABytes + p.b_bytes, &blo_map, kb * kTcBK, sg * p.Np,
+                      full0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
       }
     }
@@ -232,141 +315,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t idesc = tf32_idesc(p.Np);
       int s = 0;
       uint32_t ph = 0;
-      for (int kb = 0; kb < p.nkb && !bad; ++kb) {
-        if (!mbar_wait_bounded(full0 + 8 * s, ph) || !mbar_wait_bounded(split0 + 8 * s, ph)) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x, ++it) {
+        const int bsel = it & 1;
+        if (it >= 2 && !mbar_wait_bounded(tempty0 + 8 * bsel, ((it >> 1) - 1) & 1)) {
           bad = true;
           break;
         }
         tc_fence_after();
-        const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
-        const uint32_t a_hi = st, a_lo = st + kTcABytes, b_hi = st + 2 * kTcABytes,
-                       b_lo = b_hi + p.b_bytes;
+        const uint32_t tacc = tmem + (uint32_t)bsel * acc_cols;
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          if (!mbar_wait_bounded(full0 + 8 * s, ph) || !mbar_wait_bounded(split0 + 8 * s, ph)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
+          const uint32_t a_hi = st, a_lo = st + kTcABytes, b_hi = st + 2 * kTcABytes,
+                         b_lo = b_hi + p.b_bytes;
 #pragma unroll
-        for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 32 bytes
-          const uint32_t off = 32u * j;
-          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
-                   (kb | j) != 0);
-          mma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
-          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+          for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 32 bytes
+            const uint32_t off = 32u * j;
+            mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
+                     (kb | j) != 0);
+            mma_tf32(tacc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+            mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+          }
+          mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
-        mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
+        if (bad) break;
+        mma_commit(tfull0 + 8 * bsel);  // accumulator complete
+      }
+    }
+  } else if (warp < 6) {
+    // split each A block into tf32 hi (in place) and lo parts; zero columns >= K_s
+    const int t = threadIdx.x - 64;
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x) {
+      const int sg = p.tile_seg[tile];
+      const int Ks = p.segK ? p.segK[sg] : p.K;
+      for (int kb = 0; kb < p.nkb; ++kb) {
+        if (!mbar_wait_bounded(full0 + 8 * s, ph)) {
+          bad = true;
+          break;
+        }
+        float4* a = reinterpret_cast<float4*>(smem + (size_t)s * p.stage_bytes);
+        float4* alo = a + kTcABytes / 16;
+#pragma unroll 4
+        for (int q = t; q < (int)(kTcABytes / 16); q += 128) {
+          const int r = q >> 3;
+          const int lc = (q & 7) ^ (r & 7);  // logical 16-byte chunk under the 128-byte swizzle
+          const int k0 = kb * kTcBK + lc * 4;
+          const float4 v = a[q];
+          float4 h, l;
+          h.x = k0 < Ks ? rna_tf32(v.x) : 0.f;
+          h.y = k0 + 1 < Ks ? rna_tf32(v.y) : 0.f;
+          h.z = k0 + 2 < Ks ? rna_tf32(v.z) : 0.f;
+          h.w = k0 + 3 < Ks ? rna_tf32(v.w) : 0.f;
+          l.x = k0 < Ks ? rna_tf32(v.x - h.x) : 0.f;
+          l.y = k0 + 1 < Ks ? rna_tf32(v.y - h.y) : 0.f;
+          l.z = k0 + 2 < Ks ? rna_tf32(v.z - h.z) : 0.f;
+          l.w = k0 + 3 < Ks ? rna_tf32(v.w - h.w) : 0.f;
+          a[q] = h;
+          alo[q] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+        mbar_arrive(split0 + 8 * s);
         if (++s == S) {
           s = 0;
           ph ^= 1u;
         }
       }
-      if (!bad) mma_commit(accb);
     }
   } else {
-    // split the A block into tf32 hi (in place) and lo parts; zero columns >= K_s
-    const int t = threadIdx.x - 64;
-    int s = 0;
-    uint32_t ph = 0;
-    for (int kb = 0; kb < p.nkb && !bad; ++kb) {
-      if (!mbar_wait_bounded(full0 + 8 * s, ph)) {
-        bad = true;
-        break;
-      }
-      float4* a = reinterpret_cast<float4*>(smem + (size_t)s * p.stage_bytes);
-      float4* alo = a + kTcABytes / 16;
-#pragma unroll 4
-      for (int q = t; q < (int)(kTcABytes / 16); q += 128) {
-        const int r = q >> 3;
-        const int lc = (q & 7) ^ (r & 7);  // logical 16-byte chunk under the 128-byte swizzle
-        const int k0 = kb * kTcBK + lc * 4;
-        const float4 v = a[q];
-        float4 h, l;
-        h.x = k0 < Ks ? rna_tf32(v.x) : 0.f;
-        h.y = k0 + 1 < Ks ? rna_tf32(v.y) : 0.f;
-        h.z = k0 + 2 < Ks ? rna_tf32(v.z) : 0.f;
-        h.w = k0 + 3 < Ks ? rna_tf32(v.w) : 0.f;
-        l.x = k0 < Ks ? rna_tf32(v.x - h.x) : 0.f;
-        l.y = k0 + 1 < Ks ? rna_tf32(v.y - h.y) : 0.f;
-        l.z = k0 + 2 < Ks ? rna_tf32(v.z - h.z) : 0.f;
-        l.w = k0 + 3 < Ks ? rna_tf32(v.w - h.w) : 0.f;
-        a[q] = h;
-        alo[q] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
-      mbar_arrive(split0 + 8 * s);
-      if (++s == S) {
-        s = 0;
-        ph ^= 1u;
-      }
-    }
-    // epilogue: this warp's quarter of the accumulator lanes = rows
-    bad = __any_sync(0xffffffffu, bad) || !mbar_wait_bounded(accb, 0);
-    bad = __any_sync(0xffffffffu, bad);
-    if (!bad) {
+    // epilogue
+    const int quad = warp & 3;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+      const int bsel = it & 1;
+      bad = bad || !mbar_wait_bounded(tfull0 + 8 * bsel, (it >> 1) & 1);
+      bad = __any_sync(0xffffffffu, bad);
+      if (bad) break;
       tc_fence_after();
-      const int quad = warp & 3;
-      const int r = quad * 32 + lane;
-      const int64_t gm = row0 + r;
-      const bool valid = r < nrows;
-      Best b{-INFINITY, 0x7fffffff, -INFINITY};
-      for (int c0 = 0; c0 < p.Np; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-        if (!valid) continue;
-        if constexpr (ARGMAX) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (c0 + j < Ns) push_best(b, v[j], c0 + j);
-        } else {
-          float* crow = p.C + gm * p.ldc;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int gn = c0 + j;
-            float x = v[j];
-            if (gn < Ns) {
-              switch (p.epi) {
-                case (int)Epi::Relu: x = fmaxf(x, 0.f); break;
-                case (int)Epi::SignRelu: x = fmaxf(p.sign[sg * p.sign_seg + gn] * x, 0.f); break;
-                case (int)Epi::Sign: x = p.sign[sg * p.sign_seg + gn] * x; break;
-                case (int)Epi::PhiUpdate: {
-                  const float pv = p.aux[gm * p.ldaux + gn];
-                  const float phi = p.aux2[gm * p.ldaux2 + gn];
-                  x = x > 0.f ? phi * sqrtf(fmaxf(pv, 0.f) / x) : 0.f;
-                  break;
-                }
-                default: break;
-              }
-            }
-            v[j] = x;
-          }
-          // 16-byte stores where four columns are in range (ldc is a multiple of 4)
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const int gn = c0 + j;
-            if (gn + 3 < Ns) {
-              *reinterpret_cast<float4*>(crow + gn) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                if (gn + q < Ns) crow[gn + q] = v[j + q];
-            }
-          }
-        }
-      }
-      if constexpr (ARGMAX) {
-        int changed = 0;
-        float mg = INFINITY;
-        if (valid) {
-          mg = Ns > 1 ? b.v - b.s : INFINITY;
-          if (!p.first && p.labels[gm] != b.i) changed = 1;
-          p.labels[gm] = b.i;
-          if (p.margin) p.margin[gm] = mg;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          changed += __shfl_xor_sync(0xffffffffu, changed, o);
-          mg = fminf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
-        }
-        if (lane == 0) {
-          if (changed) atomicAdd(p.changes + sg, changed);
-          if (mg < INFINITY) atomicMin(p.minbits + sg, __float_as_uint(fmaxf(mg, 0.f)));
-        }
-      }
+      const int sg = p.tile_seg[tile];
+      const int Ns = p.segN ? p.segN[sg] : p.N;
+      tc_epilogue_row<ARGMAX>(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, sg,
+                              p.tile_row0[tile], p.tile_rows[tile], Ns);
+      tc_fence_before();
+      mbar_arrive(tempty0 + 8 * bsel);  // this buffer may take the next accumulator
     }
   }
   if (bad) atomicExch(&g_tc_wait_err, 1);
@@ -477,16 +518,17 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   p.b_bytes = (uint32_t)Np * kTcBK * 4;
   p.stage_bytes = 2 * kTcABytes + 2 * p.b_bytes;  // multiple of 1024
   p.stages = (int)std::max<int64_t>(2, std::min<int64_t>(4, (200 * 1024) / p.stage_bytes));
-  p.tmem_cols = 32;
-  while ((int)p.tmem_cols < Np) p.tmem_cols *= 2;
-  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 8 * (3 * p.stages + 1);
+  p.tmem_cols = 64;  // two accumulator buffers of a power of two >= 32 columns each
+  while ((int)p.tmem_cols < 2 * Np) p.tmem_cols *= 2;
+  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 8 * (3 * p.stages + 4);
   if (smem > 227 * 1024) return ABG_OK;
   const void* fn = a.argmax ? (const void*)k_tc_nn<true> : (const void*)k_tc_nn<false>;
   ABG_TRY(raise_smem_limit(fn, smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(rs.n_tiles, num_sms());
   if (a.argmax)
-    k_tc_nn<true><<<(unsigned)rs.n_tiles, kTcThreads, smem, s>>>(amap, hmap, lmap, p);
+    k_tc_nn<true><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
   else
-    k_tc_nn<false><<<(unsigned)rs.n_tiles, kTcThreads, smem, s>>>(amap, hmap, lmap, p);
+    k_tc_nn<false><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
   note_launch();
   note_tc_launch();
   ABG_LAUNCH_CHECK();
