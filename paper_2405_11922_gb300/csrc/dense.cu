@@ -450,6 +450,11 @@ int gemm_tn(const RowSpace& rs, const TN& a, cudaStream_t s) {
   Scratch scr(s);
   float* part;
   ABG_TRY(scr.get(&part, (size_t)rs.n_chunks * a.K * a.N));
+  bool tc = false;
+  ABG_TRY(tc_gemm_tn(rs, a, part, s, &tc));
+  if (tc)
+    return reduce_pieces<float>(rs, false, part, (int64_t)a.K * a.N, a.N, a.segK, a.K, a.segN,
+                                a.N, a.C, a.ldc, a.c_seg, s);
   const int TNv = a.N <= 32 ? 2 : (a.N <= 64 ? 4 : 8);
   dim3 grid((unsigned)rs.n_chunks, (unsigned)ceil_div(a.K, 128), (unsigned)ceil_div(a.N, 16 * TNv));
 #define ABG_TN_CASE(tn)                                                                          \

@@ -140,6 +140,10 @@ int gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s);
 // the shape or layout is outside its limits (N <= 256, 16-byte rows, no sin/cos epilogue)
 // or ABG_TENSOR_CORES=0 is set in the environment.
 int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used);
+// Chunk partials part[c][K][N] (fp32) of a TN product on the tensor cores; *used = false
+// when outside its limits (K, N <= 256, 16-byte rows) or ABG_TENSOR_CORES=0.
+struct TN;
+int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used);
 // Reads and clears the tensor-core kernels' wait flag (synchronises s).
 int tc_wait_flag(cudaStream_t s, int* flag);
 // C_s (K_s x N_s, FP64, at C + s*c_seg, row stride ldc) = A^T B over the rows of segment s.

@@ -421,6 +421,239 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// TN: partial[c] (K x N, fp32) = A[rows of chunk c]^T B[rows of chunk c], the
+// reduction running over the tall rows. Both operands need the row index as the
+// UMMA K dimension, so the split warps also transpose: each 32-row block of A
+// and B arrives row-major (TMA, no swizzle) and is written as K-major 128-byte
+// swizzled tf32 hi / lo tiles (A: up to two 128-row M blocks covering K <= 256;
+// B: Np rows). Persistent over the chunks of the row space; the chunk partials
+// are then summed in FP64 in chunk order (reduce_pieces), as for the SIMT kernel.
+//   warp 0: TMA producer (raw A, B rows)   warp 1: TMEM owner + MMA issuer
+//   warps 2-5: transpose + split           warps 6-9: epilogue (partials to global)
+// ---------------------------------------------------------------------------
+struct TnArgs {
+  int K, N;          // largest K_s (columns of A), N_s (columns of B)
+  int Np;            // UMMA N
+  int mblk;          // 128-row M blocks covering K
+  int ka_box, nb_box;  // raw tile widths (multiples of 4)
+  const int* segK;
+  const int* segN;
+  const int* chunk_seg;
+  const int64_t* chunk_row0;
+  const int* chunk_rows;
+  float* part;       // [chunk][K][N]
+  int stages;
+  uint32_t raw_bytes, raw_a_bytes;  // one raw stage, its A part
+  uint32_t op_bytes;                // the operand set (A hi, A lo, B hi, B lo)
+  uint32_t tmem_cols;
+};
+
+constexpr int kTnRows = 32;  // rows per block = UMMA K extent of one operand set
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_tn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+            const TnArgs p, int64_t n_chunks) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = p.stages;
+  unsigned char* ops = smem;                                   // operand set (1024-aligned)
+  unsigned char* raw = smem + p.op_bytes;                      // raw stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * p.raw_bytes);
+  const uint32_t rfull0 = smem_addr(bars), rempty0 = rfull0 + 8 * S, opfull = rfull0 + 16 * S,
+                 opempty = opfull + 8, tfull = opfull + 16, tempty = opfull + 24;
+  const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128, b_hi_bytes = (uint32_t)p.Np * 128;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(rfull0 + 8 * i, 1);
+      mbar_init(rempty0 + 8 * i, 128);
+    }
+    mbar_init(opfull, 128);
+    mbar_init(opempty, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t n = 0;
+      for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+        const int64_t r0 = p.chunk_row0[c];
+        const int nb = (p.chunk_rows[c] + kTnRows - 1) / kTnRows;
+        for (int b = 0; b < nb; ++b, ++n) {
+          if (n >= S && !mbar_wait_bounded(rempty0 + 8 * s, ph ^ 1u)) {
+            bad = true;
+            break;
+          }
+          const uint32_t st = smem_addr(raw + (size_t)s * p.raw_bytes);
+          mbar_expect_tx(rfull0 + 8 * s, p.raw_bytes);
+          tma_load_2d(st, &amap, 0, (int)(r0 + b * kTnRows), rfull0 + 8 * s);
+          tma_load_2d(st + p.raw_a_bytes, &bmap, 0, (int)(r0 + b * kTnRows), rfull0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = tf32_idesc(p.Np);
+      const uint32_t ob = smem_addr(ops);
+      const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes, b_hi = ob + 2 * a_hi_bytes,
+                     b_lo = b_hi + b_hi_bytes;
+      uint32_t op_ph = 0;
+      int it = 0;
+      for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x, ++it) {
+        if (it >= 1 && !mbar_wait_bounded(tempty, (it - 1) & 1)) {  // partial read out
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const int nb = (p.chunk_rows[c] + kTnRows - 1) / kTnRows;
+        for (int b = 0; b < nb; ++b) {
+          if (!mbar_wait_bounded(opfull, op_ph)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          for (int mb = 0; mb < p.mblk; ++mb) {
+            const uint32_t dcol = tmem + (uint32_t)(mb * p.Np);
+            const uint32_t ao = (uint32_t)mb * kTcM * 128;
+#pragma unroll
+            for (int j = 0; j < kTnRows / 8; ++j) {
+              const uint32_t off = 32u * j;
+              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_hi + off), idesc,
+                       (b | j) != 0);
+              mma_tf32(dcol, sw128_desc(a_lo + ao + off), sw128_desc(b_hi + off), idesc, 1u);
+              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_lo + off), idesc, 1u);
+            }
+          }
+          mma_commit(opempty);  // the operand set may be rewritten
+          op_ph ^= 1u;
+        }
+        if (bad) break;
+        mma_commit(tfull);
+      }
+    }
+  } else if (warp < 6) {
+    // transpose + split: A_raw[m][ka] -> A_op[ka][m] (K-major, 128B swizzle), same for B
+    const int t = threadIdx.x - 64;
+    const uint32_t a_rows = (uint32_t)p.mblk * kTcM;
+    int s = 0;
+    uint32_t ph = 0, op_ph = 0;
+    int64_t n = 0;
+    for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+      const int sg = p.chunk_seg[c];
+      const int Ks = p.segK ? p.segK[sg] : p.K;
+      const int Ns = p.segN ? p.segN[sg] : p.N;
+      const int rows = p.chunk_rows[c];
+      const int nb = (rows + kTnRows - 1) / kTnRows;
+      for (int b = 0; b < nb; ++b, ++n) {
+        if (!mbar_wait_bounded(rfull0 + 8 * s, ph) ||
+            (n >= 1 && !mbar_wait_bounded(opempty, op_ph ^ 1u))) {
+          bad = true;
+          break;
+        }
+        const float* ra = reinterpret_cast<const float*>(raw + (size_t)s * p.raw_bytes);
+        const float* rb = reinterpret_cast<const float*>(raw + (size_t)s * p.raw_bytes +
+                                                         p.raw_a_bytes);
+        const int mvalid = rows - b * kTnRows;  // rows of this block inside the chunk
+        auto emit = [&](const float* src, int ld, int lim, uint32_t rows_out, unsigned char* hi,
+                        unsigned char* lo) {
+          // output unit q: operand row rr (= column of src), 4 consecutive source rows m4*4..+3
+          for (uint32_t q = t; q < rows_out * 8; q += 128) {
+            const int rr = (int)(q >> 3) + 0, m4 = (int)(q & 7);
+            const int blk = rr >> 7, rl = rr & 127;
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int m = m4 * 4 + e;
+              v[e] = (rr < lim && m < mvalid) ? src[m * ld + rr] : 0.f;
+            }
+            float4 h, l;
+            h.x = rna_tf32(v[0]);
+            h.y = rna_tf32(v[1]);
+            h.z = rna_tf32(v[2]);
+            h.w = rna_tf32(v[3]);
+            l.x = rna_tf32(v[0] - h.x);
+            l.y = rna_tf32(v[1] - h.y);
+            l.z = rna_tf32(v[2] - h.z);
+            l.w = rna_tf32(v[3] - h.w);
+            const uint32_t off =
+                (uint32_t)blk * kTcM * 128 + (uint32_t)rl * 128 + (uint32_t)((m4 ^ (rl & 7)) * 16);
+            *reinterpret_cast<float4*>(hi + off) = h;
+            *reinterpret_cast<float4*>(lo + off) = l;
+          }
+        };
+        emit(ra, p.ka_box, Ks, a_rows, ops, ops + a_hi_bytes);
+        emit(rb, p.nb_box, Ns, (uint32_t)p.Np, ops + 2 * a_hi_bytes,
+             ops + 2 * a_hi_bytes + b_hi_bytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+        mbar_arrive(rempty0 + 8 * s);
+        mbar_arrive(opfull);
+        op_ph ^= 1u;
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  } else {
+    // epilogue: M block rows -> partial rows (K index), N columns
+    const int quad = warp & 3;
+    int it = 0;
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
+      bad = bad || !mbar_wait_bounded(tfull, it & 1);
+      bad = __any_sync(0xffffffffu, bad);
+      if (bad) break;
+      tc_fence_after();
+      float* pc = p.part + c * (int64_t)p.K * p.N;
+      for (int mb = 0; mb < p.mblk; ++mb) {
+        const int ka = mb * kTcM + quad * 32 + lane;
+        for (int c0 = 0; c0 < p.Np; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mb * p.Np + c0), v);
+          if (ka >= p.K) continue;
+          float* prow = pc + (int64_t)ka * p.N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < p.N) prow[c0 + j] = v[j];
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty);
+    }
+  }
+  if (bad) atomicExch(&g_tc_wait_err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
 bool tc_disabled() {
   const char* e = std::getenv("ABG_TENSOR_CORES");
   return e && e[0] == '0';
@@ -529,6 +762,70 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
     k_tc_nn<true><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
   else
     k_tc_nn<false><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+  note_launch();
+  note_tc_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
+int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used) {
+  *used = false;
+  if (tc_disabled() || a.K > 256 || a.N > 256 || rs.n_chunks == 0) return ABG_OK;
+  if (a.lda % 4 != 0 || a.ldb % 4 != 0 || reinterpret_cast<uintptr_t>(a.A) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(a.B) % 16 != 0 || rs.rows > INT32_MAX)
+    return ABG_OK;
+  const auto enc = tensor_map_encoder();
+  if (!enc) return ABG_OK;
+  TnArgs p{};
+  p.K = a.K;
+  p.N = a.N;
+  p.Np = (int)round_up(a.N, 16);
+  p.mblk = (int)ceil_div(a.K, kTcM);
+  p.ka_box = (int)round_up(a.K, 4);
+  p.nb_box = (int)round_up(a.N, 4);
+  p.segK = a.segK;
+  p.segN = a.segN;
+  p.chunk_seg = rs.chunk_seg;
+  p.chunk_row0 = rs.chunk_row0;
+  p.chunk_rows = rs.chunk_rows;
+  p.part = part;
+  p.raw_a_bytes = (uint32_t)round_up((int64_t)kTnRows * p.ka_box * 4, 128);
+  p.raw_bytes = p.raw_a_bytes + (uint32_t)round_up((int64_t)kTnRows * p.nb_box * 4, 128);
+  p.op_bytes = 2u * p.mblk * kTcM * 128 + 2u * p.Np * 128;
+  p.tmem_cols = 32;
+  while ((int)p.tmem_cols < p.mblk * p.Np) p.tmem_cols *= 2;
+  if (p.tmem_cols > 512) return ABG_OK;
+  size_t smem = 0;
+  for (p.stages = 4; p.stages >= 2; --p.stages) {
+    smem = 1024 + p.op_bytes + (size_t)p.stages * p.raw_bytes + 8 * (2 * p.stages + 4);
+    if (smem <= 220 * 1024) break;
+  }
+  if (p.stages < 2) return ABG_OK;
+  CUtensorMap amap, bmap;
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.lda * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)p.ka_box, (cuuint32_t)kTnRows};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.A), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.N, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.ldb * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)p.nb_box, (cuuint32_t)kTnRows};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&bmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.B), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  ABG_TRY(raise_smem_limit((const void*)k_tc_tn, smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(rs.n_chunks, num_sms());
+  k_tc_tn<<<grid, kTcThreads, smem, s>>>(amap, bmap, p, rs.n_chunks);
   note_launch();
   note_tc_launch();
   ABG_LAUNCH_CHECK();
