@@ -475,7 +475,9 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
     }
     if (rotated && lane == 0) atomicOr(&s_rot, 1);
     __syncthreads();
-    if (s_rot == 0) break;
+    const bool done = s_rot == 0;
+    __syncthreads();  // every thread has read the flag before thread 0 resets it
+    if (done) break;
   }
   // sigma_j^2 = |w_j|^2 (one warp per column), then rank descending (ties by index)
   __syncthreads();

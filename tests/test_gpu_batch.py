@@ -74,3 +74,35 @@ def test_batch_rejects_mixed_attribute_kinds():
     with pytest.raises(abg.AbgError) as e:
         abg.abg_batch_create([g1, g2])
     assert e.value.status == abg.ABG_EINVAL
+
+
+def test_many_segments_repeatable():
+    # hundreds of segments keep hundreds of one-CTA-per-segment kernels in flight at once:
+    # the batch must give the same bits twice, and the same bits as solving alone
+    rng = np.random.default_rng(7)
+    graphs, params = [], []
+    for i in range(300):
+        n_u = int(rng.integers(40, 400))
+        k = int(rng.integers(2, 12))
+        graphs.append(synth.make_small(2000 + i, n_u=n_u, n_v=int(1.4 * n_u), k=k, d_u=24,
+                                       deg=5, x_kind="csr_f32" if i % 2 else "dense_f32",
+                                       signal=3.0))
+        params.append(abg.params(k=k, alpha=0.6, gamma=4, d=10, t_f=4, t_g=8, seed=i))
+    for kind in ("dense_f32", "csr_f32"):
+        idx = [i for i, g in enumerate(graphs) if g.x_kind == kind]
+        gs, ps = [graphs[i] for i in idx], [params[i] for i in idx]
+        runs = []
+        for _ in range(2):
+            b = abg.abg_batch_create(gs)
+            lab, res = abg.abg_batch_cluster(b, ps)
+            b.close()
+            runs.append((lab, [r.objective for r in res]))
+        assert np.array_equal(runs[0][0], runs[1][0])
+        assert runs[0][1] == runs[1][1]
+        row = 0
+        for j, (g, p) in enumerate(zip(gs, ps)):
+            if j % 15 == 0:
+                lab1, r1 = _alone(g, p)
+                assert np.array_equal(runs[0][0][row:row + g.n_u], lab1)
+                assert runs[0][1][j] == r1.objective
+            row += g.n_u
