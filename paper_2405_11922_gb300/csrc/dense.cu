@@ -639,7 +639,7 @@ __global__ void k_cluster_sums(const int64_t* __restrict__ chunk_row0,
   const int gm = col0 + m;
   const bool active = m < wtile && gm < w;
   const bool counter = threadIdx.x == 0 && col0 == 0;
-  constexpr int U = 8;
+  constexpr int U = 32;  // rows whose loads are in flight together (adds stay in row order)
   int64_t r = r0;
   for (; r + U <= r1; r += U) {
     int l[U];

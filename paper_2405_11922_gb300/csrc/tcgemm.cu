@@ -445,11 +445,15 @@ struct TnArgs {
   float* part;       // [chunk][K][N]
   int stages;
   uint32_t raw_bytes, raw_a_bytes;  // one raw stage, its A part
-  uint32_t op_bytes;                // the operand set (A hi, A lo, B hi, B lo)
+  uint32_t op_bytes;                // one operand set (A hi, A lo, B hi, B lo)
+  int nops;                         // operand sets (2: split of block b+1 overlaps MMAs of b)
   uint32_t tmem_cols;
 };
 
 constexpr int kTnRows = 32;  // rows per block = UMMA K extent of one operand set
+#ifndef ABG_TN_NOPS
+#define ABG_TN_NOPS 2
+#endif
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_tn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
@@ -460,19 +464,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ uint32_t tmem_slot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = p.stages;
-  unsigned char* ops = smem;                                   // operand set (1024-aligned)
-  unsigned char* raw = smem + p.op_bytes;                      // raw stages
+  const int NO = p.nops;
+  unsigned char* ops = smem;                                   // operand sets (1024-aligned)
+  unsigned char* raw = smem + (size_t)NO * p.op_bytes;         // raw stages
   uint64_t* bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * p.raw_bytes);
-  const uint32_t rfull0 = smem_addr(bars), rempty0 = rfull0 + 8 * S, opfull = rfull0 + 16 * S,
-                 opempty = opfull + 8, tfull = opfull + 16, tempty = opfull + 24;
+  const uint32_t rfull0 = smem_addr(bars), rempty0 = rfull0 + 8 * S, opfull0 = rfull0 + 16 * S,
+                 opempty0 = opfull0 + 8 * NO, tfull = opempty0 + 8 * NO, tempty = tfull + 8;
   const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128, b_hi_bytes = (uint32_t)p.Np * 128;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(rfull0 + 8 * i, 1);
       mbar_init(rempty0 + 8 * i, 128);
     }
-    mbar_init(opfull, 128);
-    mbar_init(opempty, 1);
+    for (int i = 0; i < NO; ++i) {
+      mbar_init(opfull0 + 8 * i, 128);
+      mbar_init(opempty0 + 8 * i, 1);
+    }
     mbar_init(tfull, 1);
     mbar_init(tempty, 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -517,9 +524,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       const uint32_t idesc = tf32_idesc(p.Np);
-      const uint32_t ob = smem_addr(ops);
-      const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes, b_hi = ob + 2 * a_hi_bytes,
-                     b_lo = b_hi + b_hi_bytes;
+      int os = 0;  // operand set of the next block, and its phase
       uint32_t op_ph = 0;
       int it = 0;
       for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x, ++it) {
@@ -530,11 +535,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         const int nb = (p.chunk_rows[c] + kTnRows - 1) / kTnRows;
         for (int b = 0; b < nb; ++b) {
-          if (!mbar_wait_bounded(opfull, op_ph)) {
+          if (!mbar_wait_bounded(opfull0 + 8 * os, op_ph)) {
             bad = true;
             break;
           }
           tc_fence_after();
+          const uint32_t ob = smem_addr(ops + (size_t)os * p.op_bytes);
+          const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes, b_hi = ob + 2 * a_hi_bytes,
+                         b_lo = b_hi + b_hi_bytes;
           for (int mb = 0; mb < p.mblk; ++mb) {
             const uint32_t dcol = tmem + (uint32_t)(mb * p.Np);
             const uint32_t ao = (uint32_t)mb * kTcM * 128;
@@ -547,8 +555,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_lo + off), idesc, 1u);
             }
           }
-          mma_commit(opempty);  // the operand set may be rewritten
-          op_ph ^= 1u;
+          mma_commit(opempty0 + 8 * os);  // the operand set may be rewritten
+          if (++os == NO) {
+            os = 0;
+            op_ph ^= 1u;
+          }
         }
         if (bad) break;
         mma_commit(tfull);
@@ -558,7 +569,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // transpose + split: A_raw[m][ka] -> A_op[ka][m] (K-major, 128B swizzle), same for B
     const int t = threadIdx.x - 64;
     const uint32_t a_rows = (uint32_t)p.mblk * kTcM;
-    int s = 0;
+    int s = 0, os = 0;
     uint32_t ph = 0, op_ph = 0;
     int64_t n = 0;
     for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
@@ -569,7 +580,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int nb = (rows + kTnRows - 1) / kTnRows;
       for (int b = 0; b < nb; ++b, ++n) {
         if (!mbar_wait_bounded(rfull0 + 8 * s, ph) ||
-            (n >= 1 && !mbar_wait_bounded(opempty, op_ph ^ 1u))) {
+            (n >= NO && !mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u))) {
           bad = true;
           break;
         }
@@ -581,36 +592,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         unsigned char* lo) {
           // output unit q: operand row rr (= column of src), 4 consecutive source rows m4*4..+3
           for (uint32_t q = t; q < rows_out * 8; q += 128) {
-            const int rr = (int)(q >> 3) + 0, m4 = (int)(q & 7);
-            const int blk = rr >> 7, rl = rr & 127;
-            float v[4];
+            const int rr = (int)(q >> 3), m4 = (int)(q & 7);
+            {
+              const int blk = rr >> 7, rl = rr & 127;
+              float v[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int m = m4 * 4 + e;
-              v[e] = (rr < lim && m < mvalid) ? src[m * ld + rr] : 0.f;
+              for (int e = 0; e < 4; ++e) {
+                const int m = m4 * 4 + e;
+                v[e] = (rr < lim && m < mvalid) ? src[m * ld + rr] : 0.f;
+              }
+              float4 h, l;
+              h.x = rna_tf32(v[0]);
+              h.y = rna_tf32(v[1]);
+              h.z = rna_tf32(v[2]);
+              h.w = rna_tf32(v[3]);
+              l.x = rna_tf32(v[0] - h.x);
+              l.y = rna_tf32(v[1] - h.y);
+              l.z = rna_tf32(v[2] - h.z);
+              l.w = rna_tf32(v[3] - h.w);
+              const uint32_t off = (uint32_t)blk * kTcM * 128 + (uint32_t)rl * 128 +
+                                   (uint32_t)((m4 ^ (rl & 7)) * 16);
+              *reinterpret_cast<float4*>(hi + off) = h;
+              *reinterpret_cast<float4*>(lo + off) = l;
             }
-            float4 h, l;
-            h.x = rna_tf32(v[0]);
-            h.y = rna_tf32(v[1]);
-            h.z = rna_tf32(v[2]);
-            h.w = rna_tf32(v[3]);
-            l.x = rna_tf32(v[0] - h.x);
-            l.y = rna_tf32(v[1] - h.y);
-            l.z = rna_tf32(v[2] - h.z);
-            l.w = rna_tf32(v[3] - h.w);
-            const uint32_t off =
-                (uint32_t)blk * kTcM * 128 + (uint32_t)rl * 128 + (uint32_t)((m4 ^ (rl & 7)) * 16);
-            *reinterpret_cast<float4*>(hi + off) = h;
-            *reinterpret_cast<float4*>(lo + off) = l;
           }
         };
-        emit(ra, p.ka_box, Ks, a_rows, ops, ops + a_hi_bytes);
-        emit(rb, p.nb_box, Ns, (uint32_t)p.Np, ops + 2 * a_hi_bytes,
-             ops + 2 * a_hi_bytes + b_hi_bytes);
+        unsigned char* o = ops + (size_t)os * p.op_bytes;
+        emit(ra, p.ka_box, Ks, a_rows, o, o + a_hi_bytes);
+        emit(rb, p.nb_box, Ns, (uint32_t)p.Np, o + 2 * a_hi_bytes, o + 2 * a_hi_bytes + b_hi_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
         mbar_arrive(rempty0 + 8 * s);
-        mbar_arrive(opfull);
-        op_ph ^= 1u;
+        mbar_arrive(opfull0 + 8 * os);
+        if (++os == NO) {
+          os = 0;
+          op_ph ^= 1u;
+        }
         if (++s == S) {
           s = 0;
           ph ^= 1u;
@@ -797,11 +813,19 @@ int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, boo
   while ((int)p.tmem_cols < p.mblk * p.Np) p.tmem_cols *= 2;
   if (p.tmem_cols > 512) return ABG_OK;
   size_t smem = 0;
-  for (p.stages = 4; p.stages >= 2; --p.stages) {
-    smem = 1024 + p.op_bytes + (size_t)p.stages * p.raw_bytes + 8 * (2 * p.stages + 4);
-    if (smem <= 220 * 1024) break;
+  bool fits = false;
+  for (p.nops = ABG_TN_NOPS; p.nops >= 1 && !fits; --p.nops) {
+    for (p.stages = 4; p.stages >= 2; --p.stages) {
+      smem = 1024 + (size_t)p.nops * p.op_bytes + (size_t)p.stages * p.raw_bytes +
+             8 * (2 * p.stages + 2 * p.nops + 2);
+      if (smem <= 220 * 1024) {
+        fits = true;
+        break;
+      }
+    }
+    if (fits) break;
   }
-  if (p.stages < 2) return ABG_OK;
+  if (!fits) return ABG_OK;
   CUtensorMap amap, bmap;
   {
     const cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)rs.rows};
