@@ -176,19 +176,47 @@ using namespace abg;
 
 // ---- host helpers -----------------------------------------------------------------
 
+// First position in [0, n) where bad(i) holds (n if none), scanned by several host threads.
+template <class F>
+static int64_t first_bad(int64_t n, F bad) {
+  const int64_t kMinPerThread = int64_t(1) << 20;
+  const int nt = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)std::max(1u, std::thread::hardware_concurrency()), 32,
+                            n / kMinPerThread}));
+  if (nt == 1) {
+    for (int64_t i = 0; i < n; ++i)
+      if (bad(i)) return i;
+    return n;
+  }
+  std::vector<int64_t> found(nt, n);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      const int64_t b = n * t / nt, e = n * (t + 1) / nt;
+      for (int64_t i = b; i < e; ++i)
+        if (bad(i)) {
+          found[t] = i;
+          return;
+        }
+    });
+  for (auto& x : th) x.join();
+  return *std::min_element(found.begin(), found.end());
+}
+
 static int validate_csr(const int64_t* ptr, const int32_t* idx, const float* w, int64_t rows,
                         int64_t cols, int64_t nnz, const char* name) {
   ABG_CHECK(ptr && idx, "%s: null CSR arrays", name);
   ABG_CHECK(ptr[0] == 0 && ptr[rows] == nnz, "%s: ptr[0] must be 0 and ptr[rows] = nnz", name);
-  for (int64_t r = 0; r < rows; ++r)
-    ABG_CHECK(ptr[r + 1] >= ptr[r], "%s: ptr not monotone at row %lld", name, (long long)r);
-  for (int64_t j = 0; j < nnz; ++j)
-    ABG_CHECK(idx[j] >= 0 && idx[j] < cols, "%s: index %d out of range at %lld", name, idx[j],
-              (long long)j);
-  if (w)
-    for (int64_t j = 0; j < nnz; ++j)
-      ABG_CHECK(std::isfinite(w[j]) && w[j] > 0.f, "%s: weight %g at %lld not finite/positive",
-                name, (double)w[j], (long long)j);
+  const int64_t r = first_bad(rows, [&](int64_t i) { return ptr[i + 1] < ptr[i]; });
+  ABG_CHECK(r == rows, "%s: ptr not monotone at row %lld", name, (long long)r);
+  const int64_t j = first_bad(nnz, [&](int64_t i) { return idx[i] < 0 || idx[i] >= cols; });
+  ABG_CHECK(j == nnz, "%s: index %d out of range at %lld", name, j < nnz ? idx[j] : 0,
+            (long long)j);
+  if (w) {
+    const int64_t q = first_bad(nnz, [&](int64_t i) { return !(std::isfinite(w[i]) && w[i] > 0.f); });
+    ABG_CHECK(q == nnz, "%s: weight %g at %lld not finite/positive", name,
+              q < nnz ? (double)w[q] : 0.0, (long long)q);
+  }
   return ABG_OK;
 }
 
@@ -400,8 +428,8 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
                          "X CSR"));
     ABG_CHECK(d->x_val, "X CSR: null values");
     g->x_nnz = d->x_ptr[d->n_u];
-    for (int64_t j = 0; j < g->x_nnz; ++j)
-      ABG_CHECK(std::isfinite(d->x_val[j]), "X CSR: non-finite value at %lld", (long long)j);
+    const int64_t j = first_bad(g->x_nnz, [&](int64_t i) { return !std::isfinite(d->x_val[i]); });
+    ABG_CHECK(j == g->x_nnz, "X CSR: non-finite value at %lld", (long long)j);
   } else {
     ABG_CHECK(d->x, "dense attributes: null x");
   }
