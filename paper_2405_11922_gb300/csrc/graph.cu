@@ -127,32 +127,69 @@ int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s) {
 
 // Weighted degree of each row (Section 2.1), FP64 sums, one warp per row; then
 // the scale D^-1/2 with 0 for a zero degree.
+// D^-1/2 of one side: scale[row] = (sum of the row's weights)^-1/2, 0 for an empty row.
+// A warp takes 32 consecutive rows: a lane sums its own row when it has at most 32 edges,
+// the warp sums the longer ones together (lane-strided FP64 partials, then a shuffle tree);
+// the FP64 square roots and divisions then run on all lanes at once.
 __global__ void k_row_scale(const int64_t* __restrict__ ptr, const float* __restrict__ w,
                             int64_t rows, float* __restrict__ scale) {
-  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  int64_t b = ptr[row], e = ptr[row + 1];
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t base = row - (threadIdx.x & 31);
+  const int lane = threadIdx.x & 31;
+  if (base >= rows) return;  // whole warps
+  const bool valid = row < rows;
+  const int64_t b = valid ? ptr[row] : 0, e = valid ? ptr[row + 1] : 0;
+  const bool light = e - b <= 32;
   double acc = 0.0;
-  for (int64_t j = b + lane; j < e; j += 32) acc += w ? (double)w[j] : 1.0;
+  if (!w) {
+    acc = (double)(e - b);
+  } else {
+    if (light)
+      for (int64_t j = b; j < e; ++j) acc += (double)w[j];
+    unsigned heavy = __ballot_sync(0xffffffffu, valid && !light);
+    while (heavy) {
+      const int i = __ffs(heavy) - 1;
+      heavy &= heavy - 1;
+      const int64_t hb = __shfl_sync(0xffffffffu, b, i), he = __shfl_sync(0xffffffffu, e, i);
+      double part = 0.0;
+      for (int64_t j = hb + lane; j < he; j += 32) part += (double)w[j];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) scale[row] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == i) acc = part;
+    }
+  }
+  if (valid) scale[row] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
 }
 
-// L values (Eq. 7) of one storage order: val[e] = w[e] * s_row[row] * s_col[col[e]].
+// L values (Eq. 7) of one storage order: val[e] = w[e] * s_row[row] * s_col[col[e]]. A lane
+// takes its own row when it has at most 32 edges, the warp the longer rows together.
 __global__ void k_l_values(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                            const float* __restrict__ w, int64_t rows,
                            const float* __restrict__ s_row, const float* __restrict__ s_col,
                            float* __restrict__ val) {
-  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  int64_t b = ptr[row], e = ptr[row + 1];
-  double sr = (double)s_row[row];
-  for (int64_t j = b + lane; j < e; j += 32) {
-    double wj = w ? (double)w[j] : 1.0;
-    val[j] = (float)(wj * sr * (double)s_col[col[j]]);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t base = row - (threadIdx.x & 31);
+  const int lane = threadIdx.x & 31;
+  if (base >= rows) return;  // whole warps
+  const bool valid = row < rows;
+  const int64_t b = valid ? ptr[row] : 0, e = valid ? ptr[row + 1] : 0;
+  const bool light = e - b <= 32;
+  const double sr = valid ? (double)s_row[row] : 0.0;
+  if (valid && light)
+    for (int64_t j = b; j < e; ++j) {
+      const double wj = w ? (double)w[j] : 1.0;
+      val[j] = (float)(wj * sr * (double)s_col[col[j]]);
+    }
+  unsigned heavy = __ballot_sync(0xffffffffu, valid && !light);
+  while (heavy) {
+    const int i = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const int64_t hb = __shfl_sync(0xffffffffu, b, i), he = __shfl_sync(0xffffffffu, e, i);
+    const double hs = __shfl_sync(0xffffffffu, sr, i);
+    for (int64_t j = hb + lane; j < he; j += 32) {
+      const double wj = w ? (double)w[j] : 1.0;
+      val[j] = (float)(wj * hs * (double)s_col[col[j]]);
+    }
   }
 }
 
@@ -244,38 +281,72 @@ static void build_csc(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t* u_pt
 // heavy row), heavy rows cut into kHeavyChunk-edge chunks.
 static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_graph::Schedule& sc,
                           cudaStream_t s) {
-  std::vector<int32_t> tasks;  // (first row, one past the last row) of each light task
+  // row ranges scanned by several host threads; a task never crosses a range boundary, and
+  // results do not depend on task boundaries (every row sums its edges in edge order)
+  struct Part {
+    std::vector<int32_t> tasks;  // (first row, one past the last row) of each light task
+    std::vector<int64_t> cb;     // chunk starts
+    std::vector<int32_t> cslot;  // heavy slot (local) of each chunk
+    std::vector<int32_t> hrow;   // heavy rows
+    std::vector<int64_t> hc0;    // first chunk (local) of each heavy row
+  };
+  const int64_t kMinRows = int64_t(1) << 18;
+  const int nt = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16,
+                            rows / kMinRows}));
+  std::vector<Part> parts(nt);
+  auto scan = [&](int t) {
+    Part& P = parts[t];
+    const int64_t rb = rows * t / nt, re = rows * (t + 1) / nt;
+    int64_t t_r0 = -1, t_edges = 0;
+    auto close_task = [&](int64_t r_end) {
+      if (t_r0 >= 0) {
+        P.tasks.push_back((int32_t)t_r0);
+        P.tasks.push_back((int32_t)r_end);
+      }
+      t_r0 = -1;
+      t_edges = 0;
+    };
+    for (int64_t r = rb; r < re; ++r) {
+      const int64_t deg = ptr[r + 1] - ptr[r];
+      if (deg > kHeavyRow) {
+        close_task(r);
+        P.hc0.push_back((int64_t)P.cb.size());
+        const int32_t slot = (int32_t)P.hrow.size();
+        P.hrow.push_back((int32_t)r);
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; e += kHeavyChunk) {
+          P.cb.push_back(e);
+          P.cslot.push_back(slot);
+        }
+        continue;
+      }
+      if (t_r0 >= 0 && (r - t_r0 >= kTaskRows || t_edges + deg > kTaskEdges)) close_task(r);
+      if (t_r0 < 0) t_r0 = r;
+      t_edges += deg;
+    }
+    close_task(re);
+  };
+  if (nt == 1) {
+    scan(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(scan, t);
+    for (auto& x : th) x.join();
+  }
+  std::vector<int32_t> tasks;
   std::vector<int64_t> cb;
   std::vector<int32_t> cslot;
   std::vector<int32_t> hrow;
   std::vector<int64_t> hc0;
-  int64_t t_r0 = -1, t_edges = 0;
-  auto close_task = [&](int64_t r_end) {
-    if (t_r0 >= 0) {
-      tasks.push_back((int32_t)t_r0);
-      tasks.push_back((int32_t)r_end);
-    }
-    t_r0 = -1;
-    t_edges = 0;
-  };
-  for (int64_t r = 0; r < rows; ++r) {
-    const int64_t deg = ptr[r + 1] - ptr[r];
-    if (deg > kHeavyRow) {
-      close_task(r);
-      hc0.push_back((int64_t)cb.size());
-      const int32_t slot = (int32_t)hrow.size();
-      hrow.push_back((int32_t)r);
-      for (int64_t b = ptr[r]; b < ptr[r + 1]; b += kHeavyChunk) {
-        cb.push_back(b);
-        cslot.push_back(slot);
-      }
-      continue;
-    }
-    if (t_r0 >= 0 && (r - t_r0 >= kTaskRows || t_edges + deg > kTaskEdges)) close_task(r);
-    if (t_r0 < 0) t_r0 = r;
-    t_edges += deg;
+  for (const Part& P : parts) {
+    const int32_t slot0 = (int32_t)hrow.size();
+    const int64_t chunk0 = (int64_t)cb.size();
+    tasks.insert(tasks.end(), P.tasks.begin(), P.tasks.end());
+    cb.insert(cb.end(), P.cb.begin(), P.cb.end());
+    for (int32_t x : P.cslot) cslot.push_back(x + slot0);
+    hrow.insert(hrow.end(), P.hrow.begin(), P.hrow.end());
+    for (int64_t x : P.hc0) hc0.push_back(x + chunk0);
   }
-  close_task(rows);
   hc0.push_back((int64_t)cb.size());
   // the same tasks split by whether they hold edges (the TMA-gather kernel takes those that do)
   std::vector<int32_t> et, zt;
@@ -471,13 +542,12 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
     ABG_CUDA(cudaStreamSynchronize(s));
     ABG_CHECK(hbad == 0, "CSC does not match the CSR (%d columns differ)", hbad);
   }
-  const int wpb = 8;
-  k_row_scale<<<ceil_div(d->n_u, wpb), wpb * 32, 0, s>>>(g->u_ptr, w_dev, d->n_u, g->su); ::abg::note_launch();
-  k_row_scale<<<ceil_div(d->n_v, wpb), wpb * 32, 0, s>>>(g->v_ptr, wt_dev, d->n_v, g->sv); ::abg::note_launch();
-  k_l_values<<<ceil_div(d->n_u, wpb), wpb * 32, 0, s>>>(g->u_ptr, g->u_col, w_dev, d->n_u, g->su,
-                                                        g->sv, g->u_val); ::abg::note_launch();
-  k_l_values<<<ceil_div(d->n_v, wpb), wpb * 32, 0, s>>>(g->v_ptr, g->v_col, wt_dev, d->n_v, g->sv,
-                                                        g->su, g->v_val); ::abg::note_launch();
+  k_row_scale<<<ceil_div(d->n_u, 256), 256, 0, s>>>(g->u_ptr, w_dev, d->n_u, g->su); ::abg::note_launch();
+  k_row_scale<<<ceil_div(d->n_v, 256), 256, 0, s>>>(g->v_ptr, wt_dev, d->n_v, g->sv); ::abg::note_launch();
+  k_l_values<<<ceil_div(d->n_u, 256), 256, 0, s>>>(g->u_ptr, g->u_col, w_dev, d->n_u, g->su,
+                                                    g->sv, g->u_val); ::abg::note_launch();
+  k_l_values<<<ceil_div(d->n_v, 256), 256, 0, s>>>(g->v_ptr, g->v_col, wt_dev, d->n_v, g->sv,
+                                                    g->su, g->v_val); ::abg::note_launch();
   ABG_LAUNCH_CHECK();
 
   // attributes on the device
