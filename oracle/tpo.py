@@ -199,9 +199,26 @@ def nci_matrix(labels: np.ndarray, k: int) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (np.arange(n), labels)), shape=(n, k))
 
 
-def nci(Phi: np.ndarray, t_g: int):
+def polar(M: np.ndarray, rcond: float = 1e-5) -> np.ndarray:
+    """Orthogonal Procrustes factor of M (the T nearest to M with orthonormal columns on M's
+    range): T = U_r V_r^T from the SVD M = U S V^T, keeping the singular values above
+    rcond * s_1 (empty clusters make M rank deficient; the product is then still unique)."""
+    if M.size == 0:
+        return M.copy()
+    U, s, Vt = np.linalg.svd(M)
+    if s[0] <= 0:
+        return np.zeros_like(M)
+    r = int(np.count_nonzero(s > rcond * s[0]))
+    return U[:, :r] @ Vt[:r]
+
+
+def nci(Phi: np.ndarray, t_g: int, procrustes: bool = False, early_stop: bool = False):
     """T = I; t_g times: l* = argmax_l Phi[i].T[:, l] (Eq. 21; R11), Y by Eqs. 22-23,
-    T <- Phi^T Y. Returns labels, T, the last scores' top1-top2 margin, label changes per pass."""
+    T <- Phi^T Y (Algorithm 3), or with ``procrustes`` the orthogonal factor of Phi^T Y (the
+    constraint T T^T = I of Eq. 20 enforced exactly). With ``early_stop`` the passes end after
+    the first pass, other than the first, that changes no label: Y, hence T, is then a fixed
+    point and every later pass would repeat it. Returns labels, T, the last scores'
+    top1-top2 margin and the label changes per pass (its length = the passes run)."""
     n, k = Phi.shape
     T = np.eye(k)
     labels = np.zeros(n, dtype=np.int64)
@@ -217,7 +234,10 @@ def nci(Phi: np.ndarray, t_g: int):
         changes.append(n if prev is None else int(np.count_nonzero(labels != prev)))
         prev = labels
         Y = nci_matrix(labels, k)
-        T = np.asarray((Y.T @ Phi).T)
+        M = np.asarray((Y.T @ Phi).T)
+        T = polar(M) if procrustes else M
+        if early_stop and len(changes) > 1 and changes[-1] == 0:
+            break
     return labels.astype(np.int32), T, margin, changes
 
 
@@ -254,7 +274,8 @@ def attributes_of(g) -> np.ndarray | sp.csr_matrix:
 
 
 def tpo(g, k: int, alpha: float, gamma: int, d: int | None = None, t_f: int = 5, t_g: int = 20,
-        seed: int = 0, oversample: int = 10, power_iters: int = 4) -> dict:
+        seed: int = 0, oversample: int = 10, power_iters: int = 4, procrustes: bool = False,
+        early_stop: bool = False) -> dict:
     """Algorithms 1-3 end to end on the graph ``g`` (a synth.ABG-like object)."""
     d = g.d_u if d is None else d
     if not (1 <= d <= g.d_u):
@@ -274,7 +295,7 @@ def tpo(g, k: int, alpha: float, gamma: int, d: int | None = None, t_f: int = 5,
     Rp, r, R, clamped = random_features(Zhat, Q)
     Phi0, H0, Sigma = seed_factors(R, k, seed, oversample, power_iters)
     Phi, H = onmf(R, Phi0, H0, t_f)
-    labels, T, margin, changes = nci(Phi, t_g)
+    labels, T, margin, changes = nci(Phi, t_g, procrustes, early_stop)
     obj1, J = objective(R, labels, k)
     return dict(X=X, Z=Z, Zhat=Zhat, Q=Q, R=R, r=r, clamped=clamped, Sigma=Sigma, Phi0=Phi0,
                 H0=H0, Phi=Phi, H=H, labels=labels, T=T, margin=margin, changes=changes,

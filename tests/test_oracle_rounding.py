@@ -111,3 +111,52 @@ def test_planted_partition_recovery_config1():
     # the returned objective is the pair sum of Eq. 8 over R R^T, and the planted partition's
     # own objective is of the same order
     assert res["objective"] > 0 and np.isfinite(res["trace_obj"])
+
+
+def test_polar_is_the_nearest_orthogonal_matrix():
+    # polar decomposition M = T P with T orthogonal and P = T^T M symmetric positive
+    # semidefinite; no orthogonal matrix is closer to M (checked against random rotations)
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((5, 5))
+    T = tpo.polar(M)
+    assert np.allclose(T.T @ T, np.eye(5), atol=1e-12)
+    P = T.T @ M
+    assert np.allclose(P, P.T, atol=1e-12)
+    assert np.linalg.eigvalsh((P + P.T) / 2).min() > -1e-12
+    best = np.linalg.norm(M - T)
+    for _ in range(200):
+        Qr = np.linalg.qr(rng.standard_normal((5, 5)))[0]
+        assert np.linalg.norm(M - Qr) >= best - 1e-12
+
+
+def test_polar_rank_deficient_and_k1():
+    # an empty cluster zeroes a column of Phi^T Y: T keeps that column zero and is a partial
+    # isometry on the rest; for k = 1 the factor is the sign of the one entry
+    rng = np.random.default_rng(6)
+    M = rng.standard_normal((4, 4))
+    M[:, 2] = 0.0
+    T = tpo.polar(M)
+    assert np.allclose(T[:, 2], 0.0, atol=1e-12)
+    assert np.allclose(T @ T.T @ T, T, atol=1e-12)
+    assert np.allclose(tpo.polar(np.array([[-3.0]])), [[-1.0]])
+    assert np.allclose(tpo.polar(np.zeros((3, 3))), 0.0)
+
+
+def test_nci_procrustes_scores_and_fixed_point():
+    # with an orthogonal T the scores Phi T preserve row norms; a planted indicator converges,
+    # and early stopping ends at the first pass that changes nothing with the same labels and T
+    rng = np.random.default_rng(8)
+    n, k = 600, 5
+    truth = rng.integers(0, k, n)
+    Phi = np.abs(0.05 * rng.standard_normal((n, k)))
+    Phi[np.arange(n), truth] += 1.0
+    lab, T, _, ch = tpo.nci(Phi, 12, procrustes=True)
+    assert np.allclose(T.T @ T, np.eye(k), atol=1e-10)
+    assert np.allclose(np.linalg.norm(Phi @ T, axis=1), np.linalg.norm(Phi, axis=1))
+    assert ch[-1] == 0
+    lab2, T2, _, ch2 = tpo.nci(Phi, 12, procrustes=True, early_stop=True)
+    assert len(ch2) < 12 and ch2[-1] == 0 and all(c > 0 for c in ch2[1:-1])
+    assert np.array_equal(lab, lab2) and np.allclose(T, T2, atol=1e-12)
+    lab3, T3, _, ch3 = tpo.nci(Phi, 12, early_stop=True)
+    lab4, T4, _, _ = tpo.nci(Phi, 12)
+    assert np.array_equal(lab3, lab4) and np.allclose(T3, T4, atol=1e-12) and len(ch3) <= 12
