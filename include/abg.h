@@ -99,10 +99,19 @@ typedef struct {
  * "TPO (d = d_U)"); 1 <= d < d_u turns on the SVD reduction of Section 3.2.1.
  * alpha in [0, 1), gamma >= 0, 1 <= k <= min(|U|, 2d, 128), t_f, t_g >= 0,
  * oversample >= 0 and power_iters >= 0 configure the truncated randomized
- * SVDs (Halko-Martinsson-Tropp subspace iteration). */
+ * SVDs (Halko-Martinsson-Tropp subspace iteration). nci_flags (0 = Algorithm 3
+ * as printed) combines:
+ *   ABG_NCI_PROCRUSTES  T <- the orthogonal Procrustes factor of Phi^T Y (the
+ *                       constraint T T^T = I of Eq. 20 enforced: T = U_r V_r^T
+ *                       from Phi^T Y = U S V^T, singular values above 1e-5 s_1)
+ *   ABG_NCI_EARLY_STOP  stop after the first pass (other than the first) that
+ *                       changes no label: Y and T are then a fixed point, so
+ *                       the result equals that of all t_g passes. */
+#define ABG_NCI_PROCRUSTES 1
+#define ABG_NCI_EARLY_STOP 2
 typedef struct {
   int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
-  int32_t reserved0;
+  int32_t nci_flags;
   double alpha;
   uint64_t seed;
 } abg_params;
@@ -123,6 +132,8 @@ typedef struct {
    * gamma rounds, Eq. 2), Q and the random features (Eqs. 13-14), the SVD
    * seeding + NMF (Algorithm 2), NCI generation (Algorithm 3), the objective */
   float ms_phase[6];
+  int32_t nci_passes;       /* NCI passes run (t_g unless ABG_NCI_EARLY_STOP)   */
+  int32_t reserved;
 } abg_result;
 
 ABG_API const char* abg_strerror(int status);
@@ -256,13 +267,13 @@ ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t 
                      float* phi, int64_t ldphi, float* h, int64_t ldh, void* stream);
 
 /* Algorithm 3: T = I; t_g times l* = argmax_l Phi[i].T[:, l] (ties -> lowest
- * l), Y by Eqs. 22-23, T <- Phi^T Y. labels_out[n] (device int32),
- * margin_out[n] (device float, may be NULL: top1 - top2 of the last pass),
- * t_out[k][k] (device double, may be NULL: T after the last pass),
- * last_changes (host, may be NULL). */
+ * l), Y by Eqs. 22-23, T <- Phi^T Y (or its Procrustes factor, see
+ * nci_flags above). labels_out[n] (device int32), margin_out[n] (device float,
+ * may be NULL: top1 - top2 of the last pass), t_out[k][k] (device double, may
+ * be NULL: T after the last pass), last_changes and passes (host, may be NULL). */
 ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32_t t_g,
-                    int32_t* labels_out, float* margin_out, double* t_out,
-                    int32_t* last_changes, void* stream);
+                    int32_t nci_flags, int32_t* labels_out, float* margin_out, double* t_out,
+                    int32_t* last_changes, int32_t* passes, void* stream);
 
 /* Eq. 8 with s := R R^T through per-cluster sums (FP64): obj (host) gets
  * {objective, trace_obj}. labels must lie in [0, k). */

@@ -37,14 +37,15 @@ class abg_graph_desc(C.Structure):
 
 class abg_params(C.Structure):
     _fields_ = [("k", _i32), ("gamma", _i32), ("d", _i32), ("t_f", _i32), ("t_g", _i32),
-                ("oversample", _i32), ("power_iters", _i32), ("reserved0", _i32),
+                ("oversample", _i32), ("power_iters", _i32), ("nci_flags", _i32),
                 ("alpha", _f64), ("seed", _u64)]
 
 
 class abg_result(C.Structure):
     _fields_ = [("objective", _f64), ("trace_obj", _f64), ("min_margin", _f64),
                 ("last_changes", _i32), ("empty_clusters", _i32), ("clamped_rows", _i32),
-                ("chol_breakdowns", _i32), ("ms_phase", C.c_float * 6)]
+                ("chol_breakdowns", _i32), ("ms_phase", C.c_float * 6), ("nci_passes", _i32),
+                ("reserved", _i32)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "ms_phase" else getattr(self, f))
@@ -95,7 +96,7 @@ SIGNATURES = {
     "abg_seed_factors": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _i32, _u64, _p, _i64, _p,
                                    _i64, _p, _p]),
     "abg_onmf": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _i64, _p, _i64, _p]),
-    "abg_nci": (C.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p, _p, _p]),
+    "abg_nci": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _p, _p, _p, _p, _p]),
     "abg_objective": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
     "abg_objective_noalloc": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
 }
@@ -156,12 +157,18 @@ def _ld(t) -> int:
     return int(t.stride(0))
 
 
+ABG_NCI_PROCRUSTES = 1
+ABG_NCI_EARLY_STOP = 2
+
+
 def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5, t_g: int = 20,
-           oversample: int = 10, power_iters: int = 4, seed: int = 0) -> abg_params:
+           oversample: int = 10, power_iters: int = 4, seed: int = 0, procrustes: bool = False,
+           early_stop: bool = False) -> abg_params:
     p = abg_params()
     lib().abg_params_default(C.byref(p))
     p.k, p.alpha, p.gamma, p.d, p.t_f, p.t_g = k, alpha, gamma, d, t_f, t_g
     p.oversample, p.power_iters, p.seed = oversample, power_iters, seed
+    p.nci_flags = (ABG_NCI_PROCRUSTES if procrustes else 0) | (ABG_NCI_EARLY_STOP if early_stop else 0)
     return p
 
 
@@ -334,11 +341,15 @@ def abg_onmf(r, n: int, m: int, k: int, t_f: int, phi, h, stream=None):
                           _stream(stream)), "abg_onmf")
 
 
-def abg_nci(phi, n: int, k: int, t_g: int, labels_out, margin_out=None, t_out=None, stream=None):
+def abg_nci(phi, n: int, k: int, t_g: int, labels_out, margin_out=None, t_out=None, stream=None,
+            nci_flags: int = 0, with_passes: bool = False):
+    """Returns the label changes of the last pass (and the passes run with ``with_passes``)."""
     lc = C.c_int32(0)
-    _check(lib().abg_nci(_ptr(phi), n, k, _ld(phi), t_g, _ptr(labels_out), _ptr(margin_out),
-                         _ptr(t_out), C.byref(lc), _stream(stream)), "abg_nci")
-    return lc.value
+    np_ = C.c_int32(0)
+    _check(lib().abg_nci(_ptr(phi), n, k, _ld(phi), t_g, nci_flags, _ptr(labels_out),
+                         _ptr(margin_out), _ptr(t_out), C.byref(lc), C.byref(np_),
+                         _stream(stream)), "abg_nci")
+    return (lc.value, np_.value) if with_passes else lc.value
 
 
 def abg_objective(r, n: int, m: int, labels, k: int, stream=None) -> tuple[float, float]:

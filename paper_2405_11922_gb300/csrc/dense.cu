@@ -699,7 +699,7 @@ static int cluster_sums(const RowSpace& rs, const float* X, int w, int64_t ldx,
 // T_s[m][l] = S_s[l][m] / sqrt(n_l) for m, l < k_s (0 for an empty cluster), float stride kp.
 __global__ void k_nci_finalize(const int* __restrict__ segk, int kmax, const double* __restrict__ S,
                                int kp, float* __restrict__ T, double* __restrict__ t64,
-                               int* __restrict__ empty) {
+                               int* __restrict__ empty, double* __restrict__ mout) {
   const int sg = blockIdx.y;
   const int k = segk[sg];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -712,9 +712,49 @@ __global__ void k_nci_finalize(const int* __restrict__ segk, int kmax, const dou
     const double cnt = Ss[(int64_t)kmax * kmax + l];
     v = cnt > 0 ? Ss[(int64_t)l * kmax + m] / sqrt(cnt) : 0.0;
     if (m == 0 && cnt <= 0) atomicAdd(empty + sg, 1);
-    if (t64) t64[(int64_t)sg * kmax * kmax + m * kmax + l] = v;
+    if (t64 && !mout) t64[(int64_t)sg * kmax * kmax + m * kmax + l] = v;
   }
-  Ts[m * kp + l] = (float)v;
+  if (mout)  // Phi^T Y for the Procrustes factor (zero outside k_s x k_s)
+    mout[(int64_t)sg * kmax * kmax + (int64_t)m * kmax + l] = v;
+  else
+    Ts[m * kp + l] = (float)v;
+}
+
+// Orthogonal Procrustes factor T = U_r V_r^T of M = Phi^T Y = U S V^T (singular values above
+// 1e-5 s_1): W = M V S_r^+, then T = W V^T. evals = s^2 (descending), evecs = V (columns).
+__global__ void k_polar_w(const int* __restrict__ segk, int kmax, const double* __restrict__ M,
+                          const double* __restrict__ evals, const double* __restrict__ evecs,
+                          double* __restrict__ W) {
+  const int sg = blockIdx.y;
+  const int k = segk[sg];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kmax * kmax) return;
+  const int m = idx / kmax, j = idx % kmax;
+  const int64_t o = (int64_t)sg * kmax * kmax;
+  const double* ev = evals + (int64_t)sg * kmax;
+  double v = 0.0;
+  if (m < k && j < k && ev[0] > 0.0 && ev[j] > 1e-10 * ev[0]) {
+    double acc = 0.0;
+    for (int p = 0; p < k; ++p) acc += M[o + (int64_t)m * kmax + p] * evecs[o + (int64_t)p * kmax + j];
+    v = acc / sqrt(ev[j]);
+  }
+  W[o + (int64_t)m * kmax + j] = v;
+}
+
+__global__ void k_polar_t(const int* __restrict__ segk, int kmax, const double* __restrict__ W,
+                          const double* __restrict__ evecs, int kp, float* __restrict__ T,
+                          double* __restrict__ t64) {
+  const int sg = blockIdx.y;
+  const int k = segk[sg];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kmax * kmax) return;
+  const int m = idx / kmax, l = idx % kmax;
+  const int64_t o = (int64_t)sg * kmax * kmax;
+  double v = 0.0;
+  if (m < k && l < k)
+    for (int j = 0; j < k; ++j) v += W[o + (int64_t)m * kmax + j] * evecs[o + (int64_t)l * kmax + j];
+  if (t64 && m < k && l < k) t64[o + (int64_t)m * kmax + l] = v;
+  T[(int64_t)sg * kmax * kp + m * kp + l] = (float)v;
 }
 
 __global__ void k_nci_init(int nseg, const int* __restrict__ segk, int kmax, int kp,
@@ -738,15 +778,28 @@ __global__ void k_reset_counters(int nseg, int* __restrict__ c) {
 }
 
 int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ldphi, int t_g,
-            int32_t* labels, float* margin, double* t_out, int* counters, cudaStream_t s) {
+            int flags, int32_t* labels, float* margin, double* t_out, int* counters,
+            std::vector<int>* passes, cudaStream_t s) {
   const int kmax = ss.k_max, nseg = rs.nseg;
   ABG_CHECK(kmax >= 1 && kmax <= kMaxK, "nci: need 1 <= k <= %d", kMaxK);
+  const bool procrustes = flags & ABG_NCI_PROCRUSTES;
+  const bool early = flags & ABG_NCI_EARLY_STOP;
   Scratch scr(s);
   const int kp = (int)round_up(kmax, 4);
   float* T;
   ABG_TRY(scr.get(&T, (size_t)nseg * kmax * kp));
   double* S;
   ABG_TRY(scr.get(&S, (size_t)nseg * ((size_t)kmax * kmax + kmax)));
+  double *M = nullptr, *W = nullptr, *evals = nullptr, *evecs = nullptr;
+  if (procrustes) {
+    ABG_TRY(scr.get(&M, (size_t)nseg * kmax * kmax));
+    ABG_TRY(scr.get(&W, (size_t)nseg * kmax * kmax));
+    ABG_TRY(scr.get(&evals, (size_t)nseg * kmax));
+    ABG_TRY(scr.get(&evecs, (size_t)nseg * kmax * kmax));
+  }
+  if (passes) passes->assign(nseg, t_g);
+  std::vector<int> done(nseg, 0), host(nseg);
+  int n_done = 0;
   k_nci_init<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)nseg * kmax * kp, 256), 4096), 256, 0,
                s>>>(nseg, ss.k, kmax, kp, T);
   note_launch();
@@ -772,9 +825,28 @@ int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ld
     ABG_TRY(gemm_nn(rs, a, s));
     ABG_TRY(cluster_sums(rs, phi, kmax, ldphi, labels, kmax, S, s));
     dim3 g((unsigned)ceil_div(kmax * kmax, 256), (unsigned)nseg);
-    k_nci_finalize<<<g, 256, 0, s>>>(ss.k, kmax, S, kp, T, t_out, counters + 2 * nseg);
+    k_nci_finalize<<<g, 256, 0, s>>>(ss.k, kmax, S, kp, T, t_out, counters + 2 * nseg, M);
     note_launch();
+    if (procrustes) {
+      ABG_TRY(svd_right(nseg, kmax, ss.k, kmax, M, evals, evecs, s));
+      k_polar_w<<<g, 256, 0, s>>>(ss.k, kmax, M, evals, evecs, W);
+      note_launch();
+      k_polar_t<<<g, 256, 0, s>>>(ss.k, kmax, W, evecs, kp, T, t_out);
+      note_launch();
+    }
     ABG_LAUNCH_CHECK();
+    if (early && t >= 1) {  // a pass that changed no label leaves Y and T at a fixed point
+      ABG_CUDA(cudaMemcpyAsync(host.data(), counters, sizeof(int) * nseg, cudaMemcpyDeviceToHost,
+                               s));
+      ABG_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i < nseg; ++i)
+        if (!done[i] && host[i] == 0) {
+          done[i] = 1;
+          ++n_done;
+          if (passes) (*passes)[i] = t + 1;
+        }
+      if (n_done == nseg) break;
+    }
   }
   if (t_g == 0) ABG_CUDA(cudaMemsetAsync(labels, 0, sizeof(int32_t) * rs.rows, s));
   return ABG_OK;

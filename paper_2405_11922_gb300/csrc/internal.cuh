@@ -174,15 +174,22 @@ int nmf_update_h(int nseg, int m, const int* segk, int kmax, float* H, int64_t l
 int small_atb(int nseg, int m, const int* segk, int kmax, const double* A, int64_t lda,
               int64_t aseg, const float* H, int64_t ldh, int64_t hseg, double* C, int64_t ldc,
               int64_t cseg, cudaStream_t s);
-// Algorithm 3 (all t_g passes) per segment. counters (device, 3*nseg ints): last-pass label
-// changes, minimum margin (float bits), empty clusters.
+// Algorithm 3 per segment (t_g passes; flags = ABG_NCI_*). counters (device, 3*nseg ints):
+// last-pass label changes, minimum margin (float bits), empty clusters. passes (host,
+// optional): the passes each segment needed (t_g unless it stopped early).
 int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ldphi, int t_g,
-            int32_t* labels, float* margin, double* t_out, int* counters, cudaStream_t s);
+            int flags, int32_t* labels, float* margin, double* t_out, int* counters,
+            std::vector<int>* passes, cudaStream_t s);
 // Eq. 8 per segment: out_dev[2s] = objective, out_dev[2s+1] = Tr(Y^T R R^T Y).
 int objective(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int64_t ldr,
               const int32_t* labels, double* out_dev, cudaStream_t s);
 
 // ---- linalg.cu --------------------------------------------------------------
+// Right singular vectors and squared singular values (descending) of Bt_s (m x l_s, FP64, row
+// stride lmax inside an m*lmax slab): FP32 one-sided Jacobi, results FP64 (l_s x l_s slabs of
+// stride lmax).
+int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
+              double* evecs, cudaStream_t s);
 // Gaussian matrix (rows x cols, row stride ld) of each segment from (seeds[s], stream id); the
 // segment's block sits at out + s*oseg; columns >= cols_s (segcols) are set to 0.
 int gaussian_f64(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols, double* out,

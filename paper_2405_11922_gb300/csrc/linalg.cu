@@ -505,8 +505,8 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
   }
 }
 
-static int svd_onesided(int nseg, int m, const int* segl, int lmax, const double* Bt,
-                        double* evals, double* evecs, cudaStream_t s) {
+int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
+              double* evecs, cudaStream_t s) {
   ABG_CHECK(lmax <= kMaxRsvdBlock, "svd: block width above %d", kMaxRsvdBlock);
   Scratch scr(s);
   const size_t smem = sizeof(float) * ((size_t)m * lmax + (size_t)lmax * lmax);
@@ -674,7 +674,7 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   Y = cur;
   // B^T = A^T Q (m x l); its SVD gives sigma and the left singular vectors of B
   ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
-  ABG_TRY(svd_onesided(nseg, m, ss.l, lmax, Bt, evals, evecs, s));
+  ABG_TRY(svd_right(nseg, m, ss.l, lmax, Bt, evals, evecs, s));
   ABG_TRY(column_sums(rs, lmax, Y, ll, qsum, lmax, s));
   {
     dim3 g((unsigned)ceil_div(kmax, 128), (unsigned)nseg);

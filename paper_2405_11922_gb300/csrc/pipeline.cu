@@ -31,6 +31,8 @@ int check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d
             "need 1 <= k <= min(|U|, 2d, %d) (got k=%d)", kMaxK, p->k);
   ABG_CHECK(d == g->d_u || (int64_t)d + p->oversample <= 1024,
             "attribute reduction needs d + oversample <= 1024");
+  ABG_CHECK((p->nci_flags & ~(ABG_NCI_PROCRUSTES | ABG_NCI_EARLY_STOP)) == 0,
+            "unknown nci_flags %d", p->nci_flags);
   *d_eff = d;
   return ABG_OK;
 }
@@ -42,6 +44,7 @@ struct SolveOut {
   int* counters = nullptr;     // 3 per segment: changes, min margin bits, empty clusters
   int* clamped = nullptr;      // per segment
   int* breakdowns = nullptr;   // 1
+  std::vector<int> passes;     // NCI passes per segment
 };
 
 // Attributes the propagation reads: the graph's own (dense), a densified CSR, or the
@@ -254,7 +257,8 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   ABG_TRY(onmf_iterations(rs, ss, R, m, ldr, p.t_f, phi, kk, H, kk, hseg, s));
   if (ev) ABG_CUDA(cudaEventRecord(ev[4], s));
   // ---- Algorithm 3 ----
-  ABG_TRY(nci_run(rs, ss, phi, kk, p.t_g, o.labels, nullptr, nullptr, o.counters, s));
+  ABG_TRY(nci_run(rs, ss, phi, kk, p.t_g, p.nci_flags, o.labels, nullptr, nullptr, o.counters,
+                  &o.passes, s));
   if (ev) ABG_CUDA(cudaEventRecord(ev[5], s));
   // ---- Eq. 8 ----
   ABG_TRY(objective(rs, ss, R, m, ldr, o.labels, o.obj, s));
@@ -278,8 +282,10 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     if (i == 0) d = di;
     ABG_CHECK(di == d && ps[i].alpha == ps[0].alpha && ps[i].gamma == ps[0].gamma &&
                   ps[i].t_f == ps[0].t_f && ps[i].t_g == ps[0].t_g &&
-                  ps[i].oversample == ps[0].oversample && ps[i].power_iters == ps[0].power_iters,
-              "batched solves need the same d, alpha, gamma, t_f, t_g, oversample, power_iters");
+                  ps[i].oversample == ps[0].oversample && ps[i].power_iters == ps[0].power_iters &&
+                  ps[i].nci_flags == ps[0].nci_flags,
+              "batched solves need the same d, alpha, gamma, t_f, t_g, oversample, power_iters, "
+              "nci_flags");
   }
   ABG_CUDA(cudaSetDevice(g->device));
   const int nseg = g->nseg;
@@ -293,7 +299,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) ev[i] = e[i].e;
   std::vector<double> obj(2 * nseg);
-  std::vector<int> cnt(3 * nseg), cl(nseg);
+  std::vector<int> cnt(3 * nseg), cl(nseg), passes;
   int bd = 0;
   {
     Scratch scr(s);
@@ -308,6 +314,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     ABG_CUDA(cudaMemsetAsync(o.clamped, 0, sizeof(int) * nseg, s));
     ABG_CUDA(cudaMemsetAsync(o.breakdowns, 0, sizeof(int), s));
     ABG_TRY(solve_batch(g, rs, ks, seeds, ps[0], d, o, ev, s));
+    passes = o.passes;
     ABG_CUDA(cudaMemcpyAsync(labels, o.labels, sizeof(int32_t) * g->n_u, cudaMemcpyDefault, s));
     ABG_CUDA(cudaMemcpyAsync(obj.data(), o.obj, sizeof(double) * 2 * nseg, cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaMemcpyAsync(cnt.data(), o.counters, sizeof(int) * 3 * nseg, cudaMemcpyDeviceToHost, s));
@@ -333,6 +340,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     r.empty_clusters = ps[i].t_g > 0 ? cnt[2 * nseg + i] : ps[i].k - 1;
     r.clamped_rows = cl[i];
     r.chol_breakdowns = bd;
+    r.nci_passes = i < (int)passes.size() ? passes[i] : ps[i].t_g;
     for (int j = 0; j < 6; ++j) r.ms_phase[j] = ms[j];
     finite &= std::isfinite(r.objective);
     if (res) res[i] = r;
@@ -362,7 +370,7 @@ ABG_API void abg_params_default(abg_params* p) {
   p->t_g = 20;
   p->oversample = 10;
   p->power_iters = 4;
-  p->reserved0 = 0;
+  p->nci_flags = 0;
   p->alpha = 0.6;
   p->seed = 0;
 }
@@ -536,8 +544,8 @@ ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t 
 }
 
 ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32_t t_g,
-                    int32_t* labels_out, float* margin_out, double* t_out, int32_t* last_changes,
-                    void* stream) {
+                    int32_t nci_flags, int32_t* labels_out, float* margin_out, double* t_out,
+                    int32_t* last_changes, int32_t* passes, void* stream) {
   ABG_CHECK(phi && labels_out && n >= 1 && t_g >= 0 && k >= 1 && k <= kMaxK, "bad arguments");
   ABG_CHECK(ldphi >= k && ldphi % 4 == 0, "ldphi must be >= k and a multiple of 4");
   cudaStream_t s = (cudaStream_t)stream;
@@ -548,11 +556,15 @@ ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32
   ABG_TRY(segsizes_build(&ss, {k}, {k}, {0}, scr, s));
   int* counters;
   ABG_TRY(scr.get(&counters, 3));
-  ABG_TRY(nci_run(rs, ss, phi, ldphi, t_g, labels_out, margin_out, t_out, counters, s));
+  ABG_CHECK((nci_flags & ~(ABG_NCI_PROCRUSTES | ABG_NCI_EARLY_STOP)) == 0, "unknown nci_flags");
+  std::vector<int> np;
+  ABG_TRY(nci_run(rs, ss, phi, ldphi, t_g, nci_flags, labels_out, margin_out, t_out, counters, &np,
+                  s));
   int host[3] = {0, 0, 0};
   ABG_CUDA(cudaMemcpyAsync(host, counters, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
   ABG_CUDA(cudaStreamSynchronize(s));
   if (last_changes) *last_changes = t_g > 0 ? host[0] : 0;
+  if (passes) *passes = np.empty() ? t_g : np[0];
   return ABG_OK;
 }
 

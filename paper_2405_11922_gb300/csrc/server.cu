@@ -61,7 +61,8 @@ bool compatible(const Job& a, const Job& b) {
   const abg_params &p = a.params, &q = b.params;
   return a.desc.d_u == b.desc.d_u && a.desc.x_kind == b.desc.x_kind && p.d == q.d &&
          p.alpha == q.alpha && p.gamma == q.gamma && p.t_f == q.t_f && p.t_g == q.t_g &&
-         p.oversample == q.oversample && p.power_iters == q.power_iters;
+         p.oversample == q.oversample && p.power_iters == q.power_iters &&
+         p.nci_flags == q.nci_flags;
 }
 
 }  // namespace

@@ -106,3 +106,25 @@ def test_many_segments_repeatable():
                 assert np.array_equal(runs[0][0][row:row + g.n_u], lab1)
                 assert runs[0][1][j] == r1.objective
             row += g.n_u
+
+
+def test_batch_with_nci_flags_equals_alone():
+    # early stopping is decided per segment; a segment that has converged repeats the same pass
+    # while the others continue, so its result and its reported passes equal the solve alone
+    graphs = _graphs("dense_f32", 6, 16, 700)
+    params = [abg.params(k=g.k, alpha=0.6, gamma=4, d=16, t_f=4, t_g=15, seed=3 + i,
+                         procrustes=True, early_stop=True) for i, g in enumerate(graphs)]
+    b = abg.abg_batch_create(graphs)
+    labels, results = abg.abg_batch_cluster(b, params)
+    b.close()
+    row = 0
+    for g, p, r in zip(graphs, params, results):
+        lab1, r1 = _alone(g, p)
+        assert np.array_equal(labels[row:row + g.n_u], lab1)
+        assert r.objective == r1.objective and r.nci_passes == r1.nci_passes
+        row += g.n_u
+    mixed = [abg.params(k=2), abg.params(k=2, procrustes=True)]
+    b = abg.abg_batch_create(graphs[:2])
+    with pytest.raises(abg.AbgError):
+        abg.abg_batch_cluster(b, mixed)
+    b.close()

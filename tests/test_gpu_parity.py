@@ -356,3 +356,49 @@ def test_row_padding_is_ignored_by_every_step():
     ref_o = tpo.objective(Rm, labels.cpu().numpy(), 3)
     assert obj[0] == pytest.approx(ref_o[0], rel=1e-5)
     h.close()
+
+
+@pytest.mark.parametrize("k", [1, 3, 17, 100])
+@pytest.mark.parametrize("flags", [abg.ABG_NCI_PROCRUSTES, abg.ABG_NCI_EARLY_STOP,
+                                   abg.ABG_NCI_PROCRUSTES | abg.ABG_NCI_EARLY_STOP])
+def test_nci_variants(k, flags):
+    # the Procrustes factor (T T^T = I enforced) and early stopping at the fixed point
+    rng = np.random.default_rng(300 + k)
+    n = 2999
+    lab = rng.integers(0, k, n)
+    Phi = np.abs(0.3 * rng.standard_normal((n, k)) / np.sqrt(n))
+    Phi[np.arange(n), lab] += 1.0 / np.sqrt(n / k)
+    if k > 3:
+        Phi[:, 2] = 0.0                                  # a column nobody picks: empty cluster
+    Phi = Phi.astype(np.float32).astype(np.float64)
+    labels = torch.zeros(n, dtype=torch.int32, device=DEV)
+    margin = torch.zeros(n, dtype=torch.float32, device=DEV)
+    T = torch.zeros((k, k), dtype=torch.float64, device=DEV)
+    _, passes = abg.abg_nci(dev(Phi), n, k, 20, labels, margin, T, nci_flags=flags,
+                            with_passes=True)
+    proc = bool(flags & abg.ABG_NCI_PROCRUSTES)
+    early = bool(flags & abg.ABG_NCI_EARLY_STOP)
+    rl, rT, rm, ch = tpo.nci(Phi, 20, procrustes=proc, early_stop=early)
+    assert passes == len(ch)
+    sure = rm > 1e-4
+    assert np.array_equal(labels.cpu().numpy()[sure], rl[sure])
+    assert np.abs(T.cpu().numpy() - rT).max() < 2e-5 * max(1.0, np.abs(rT).max())
+    if proc:
+        Tg = T.cpu().numpy()
+        keep = np.abs(rT).sum(axis=0) > 1e-8        # columns of clusters that are not empty
+        assert np.allclose((Tg.T @ Tg)[np.ix_(keep, keep)], np.eye(keep.sum()), atol=1e-4)
+
+
+def test_solve_with_nci_variants(planted):
+    g, p, ref = planted
+    for proc, early in [(True, False), (False, True), (True, True)]:
+        q = abg.params(k=p["k"], alpha=p["alpha"], gamma=p["gamma"], d=p["d"], t_f=p["t_f"],
+                       t_g=p["t_g"], seed=p["seed"], procrustes=proc, early_stop=early)
+        h = abg.abg_create(g)
+        lab, res = abg.abg_cluster(h, q)
+        h.close()
+        r = tpo.tpo(g, procrustes=proc, early_stop=early, **p)
+        sure = r["margin"] > 1e-4
+        assert np.array_equal(lab[sure], r["labels"][sure])
+        assert res.objective == pytest.approx(r["objective"], rel=1e-5)
+        assert res.nci_passes == len(r["changes"])
