@@ -76,7 +76,12 @@ typedef struct abg_graph abg_graph;
  * with u_ptr[0] = 0, u_ptr[n_u] = nnz and v_idx in [0, n_v). w == NULL means
  * unit weights; weights must be finite and > 0. The CSC (v_ptr, u_idx, w_t)
  * is optional (all three NULL: it is built by a stable counting sort); when
- * given it must hold exactly the same edges. */
+ * given it must hold exactly the same edges.
+ * side: ABG_SIDE_U clusters U with attributes X_U (x rows = n_u). ABG_SIDE_V
+ * clusters V instead (the method with the roles of U and V exchanged; x then
+ * holds X_V, n_v rows, and every per-node output has n_v entries). */
+#define ABG_SIDE_U 0
+#define ABG_SIDE_V 1
 typedef struct {
   int64_t n_u, n_v, nnz;
   const int64_t* u_ptr;
@@ -92,7 +97,7 @@ typedef struct {
   const int32_t* x_idx;
   const float* x_val;
   int32_t device;
-  int32_t reserved;
+  int32_t side;
 } abg_graph_desc;
 
 /* Method parameters (Table 1). d = 0 means d = d_u (no attribute reduction,

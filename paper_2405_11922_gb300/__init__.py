@@ -32,7 +32,7 @@ class abg_graph_desc(C.Structure):
                 ("v_ptr", _p), ("u_idx", _p), ("w_t", _p),
                 ("d_u", _i32), ("x_kind", _i32),
                 ("x", _p), ("x_ptr", _p), ("x_idx", _p), ("x_val", _p),
-                ("device", _i32), ("reserved", _i32)]
+                ("device", _i32), ("side", _i32)]
 
 
 class abg_params(C.Structure):
@@ -197,9 +197,14 @@ def _host(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
-def abg_create(g, device: int = 0, stream=None, csc=None) -> Graph:
+ABG_SIDE_U = 0
+ABG_SIDE_V = 1
+
+
+def abg_create(g, device: int = 0, stream=None, csc=None, side: int = ABG_SIDE_U) -> Graph:
     """Upload an ABG. ``g`` carries n_u, n_v, u_ptr, v_idx, w, d_u, x_kind, x / x_ptr,
-    x_idx, x_val (see ``synth.ABG``). ``csc`` = optional (v_ptr, u_idx, w_t) host arrays."""
+    x_idx, x_val (see ``synth.ABG``). ``csc`` = optional (v_ptr, u_idx, w_t) host arrays.
+    ``side = ABG_SIDE_V`` clusters V: the attributes in ``g`` then describe the V nodes."""
     keep = []
 
     def h(a, dt):
@@ -225,8 +230,11 @@ def abg_create(g, device: int = 0, stream=None, csc=None) -> Graph:
     else:
         d.x_ptr, d.x_idx, d.x_val = h(g.x_ptr, np.int64), h(g.x_idx, np.int32), h(g.x_val, np.float32)
     d.device = device
+    d.side = side
     out = C.c_void_p()
     _check(lib().abg_create(C.byref(d), _stream(stream), C.byref(out)), "abg_create")
+    if side == ABG_SIDE_V:          # the clustered side comes first
+        return Graph(out.value, d.n_v, d.n_u, d.d_u)
     return Graph(out.value, d.n_u, d.n_v, d.d_u)
 
 
@@ -249,7 +257,7 @@ def abg_tensor_core_launches() -> int:
     return int(lib().abg_tensor_core_launches())
 
 
-def _desc_of(g, keep: list) -> abg_graph_desc:
+def _desc_of(g, keep: list, side: int = ABG_SIDE_U) -> abg_graph_desc:
     def h(a, dt):
         arr = _host(a, dt)
         keep.append(arr)
@@ -269,21 +277,24 @@ def _desc_of(g, keep: list) -> abg_graph_desc:
         d.x = h(g.x, np.uint16)
     else:
         d.x_ptr, d.x_idx, d.x_val = h(g.x_ptr, np.int64), h(g.x_idx, np.int32), h(g.x_val, np.float32)
+    d.side = side
     return d
 
 
-def abg_batch_create(graphs, device: int = 0, stream=None) -> Graph:
+def abg_batch_create(graphs, device: int = 0, stream=None, side: int = ABG_SIDE_U) -> Graph:
     """Stack several graphs (same d_u and attribute kind) into one batch (segments)."""
     keep = []
     arr = (abg_graph_desc * len(graphs))()
     for i, g in enumerate(graphs):
-        arr[i] = _desc_of(g, keep)
+        arr[i] = _desc_of(g, keep, side)
         arr[i].device = device
     out = C.c_void_p()
     _check(lib().abg_batch_create(arr, len(graphs), device, _stream(stream), C.byref(out)),
            "abg_batch_create")
-    return Graph(out.value, sum(int(g.n_u) for g in graphs), sum(int(g.n_v) for g in graphs),
-                 int(graphs[0].d_u))
+    nu, nv = sum(int(g.n_u) for g in graphs), sum(int(g.n_v) for g in graphs)
+    if side == ABG_SIDE_V:
+        nu, nv = nv, nu
+    return Graph(out.value, nu, nv, int(graphs[0].d_u))
 
 
 def abg_batch_cluster(batch: Graph, params_list, labels=None, stream=None):
@@ -386,16 +397,16 @@ class Server:
         self._keep = {}
         self._n_u = {}
 
-    def submit(self, g, p: abg_params) -> int:
+    def submit(self, g, p: abg_params, side: int = ABG_SIDE_U) -> int:
         keep = []
-        d = _desc_of(g, keep)
+        d = _desc_of(g, keep, side)
         rid = C.c_uint64(0)
         st = lib().abg_submit(self.handle, C.byref(d), C.byref(p), C.byref(rid))
         if st == ABG_ENOTADMITTED:
             return -int(rid.value)
         _check(st, "abg_submit")
         self._keep[rid.value] = (keep, d)
-        self._n_u[rid.value] = int(g.n_u)
+        self._n_u[rid.value] = int(g.n_v if side == ABG_SIDE_V else g.n_u)
         return int(rid.value)
 
     def poll(self, rid: int, timeout_us: int = -1):

@@ -276,6 +276,44 @@ static void build_csc(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t* u_pt
     }
 }
 
+int abg::swap_sides(const abg_graph_desc* in, abg::SideSwap* store, const abg_graph_desc** out) {
+  *out = in;
+  ABG_CHECK(in, "null descriptor");
+  ABG_CHECK(in->side == ABG_SIDE_U || in->side == ABG_SIDE_V, "side must be ABG_SIDE_U or _V");
+  if (in->side == ABG_SIDE_U) return ABG_OK;
+  // clustering V: the same edges with the roles exchanged (the CSC becomes the CSR)
+  ABG_CHECK(in->n_u >= 1 && in->n_v >= 1 && in->n_u < (1ll << 31) && in->n_v < (1ll << 31),
+            "need 1 <= |U|, |V| < 2^31");
+  ABG_CHECK(in->nnz >= 0, "nnz < 0");
+  ABG_TRY(validate_csr(in->u_ptr, in->v_idx, in->w, in->n_u, in->n_v, in->nnz, "CSR"));
+  abg_graph_desc& d = store->desc;
+  d = *in;
+  if (in->v_ptr || in->u_idx || in->w_t) {
+    ABG_CHECK(in->v_ptr && in->u_idx && (!in->w == !in->w_t),
+              "CSC needs v_ptr, u_idx and (w_t iff w)");
+  } else {
+    build_csc(in->n_u, in->n_v, in->nnz, in->u_ptr, in->v_idx, in->w, store->vp, store->ui,
+              store->wt);
+    d.v_ptr = store->vp.data();
+    d.u_idx = store->ui.data();
+    d.w_t = in->w ? store->wt.data() : nullptr;
+  }
+  const int64_t* vp = d.v_ptr;
+  const int32_t* ui = d.u_idx;
+  const float* wt = d.w_t;
+  d.n_u = in->n_v;
+  d.n_v = in->n_u;
+  d.u_ptr = vp;
+  d.v_idx = ui;
+  d.w = wt;
+  d.v_ptr = in->u_ptr;
+  d.u_idx = in->v_idx;
+  d.w_t = in->w;
+  d.side = ABG_SIDE_U;
+  *out = &d;
+  return ABG_OK;
+}
+
 // Row schedule of one SpMM direction: light rows grouped into tasks of at most
 // kTaskRows consecutive rows and about kTaskEdges edges (a task never spans a
 // heavy row), heavy rows cut into kHeavyChunk-edge chunks.
@@ -620,9 +658,13 @@ ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out
     return ABG_EINVAL;
   }
   *out = nullptr;
+  abg::SideSwap swap;
+  const abg_graph_desc* dd = nullptr;
+  int st = abg::swap_sides(desc, &swap, &dd);
+  if (st != ABG_OK) return st;
   abg_graph* g = new abg_graph();
   cudaStream_t s = (cudaStream_t)stream;
-  int st = create_impl(desc, s, g);
+  st = create_impl(dd, s, g);
   if (st != ABG_OK) {
     abg_destroy(g);
     return st;
@@ -632,14 +674,22 @@ ABG_API int abg_create(const abg_graph_desc* desc, void* stream, abg_graph** out
 }
 
 // Stack n graphs into one block-diagonal graph whose segments are the inputs.
-ABG_API int abg_batch_create(const abg_graph_desc* descs, int32_t n, int32_t device, void* stream,
-                             abg_graph** out) {
+ABG_API int abg_batch_create(const abg_graph_desc* descs_in, int32_t n, int32_t device,
+                             void* stream, abg_graph** out) {
   if (!out) {
     set_error("null output pointer");
     return ABG_EINVAL;
   }
   *out = nullptr;
-  ABG_CHECK(descs && n >= 1, "need at least one graph");
+  ABG_CHECK(descs_in && n >= 1, "need at least one graph");
+  std::vector<SideSwap> swaps(n);
+  std::vector<abg_graph_desc> dv(n);
+  for (int i = 0; i < n; ++i) {
+    const abg_graph_desc* p = nullptr;
+    ABG_TRY(swap_sides(&descs_in[i], &swaps[i], &p));
+    dv[i] = *p;
+  }
+  const abg_graph_desc* descs = dv.data();
   const int32_t d_u = descs[0].d_u, kind = descs[0].x_kind;
   int64_t nu = 0, nv = 0, nnz = 0, xnnz = 0;
   bool weighted = false;

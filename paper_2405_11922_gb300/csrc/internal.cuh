@@ -78,6 +78,15 @@ static_assert(kHeavyRow <= kTaskEdges && kTaskEdges % 4 == 0 && kTaskRows <= 32,
 int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s);
 // host-only validation of a graph descriptor (CSR, optional CSC, weights, attributes)
 int validate_desc(const abg_graph_desc* d);
+// A descriptor with side = ABG_SIDE_V seen as the equivalent ABG_SIDE_U descriptor (U and V
+// exchanged; a CSC the caller did not give is built into `store`, which must outlive *out).
+struct SideSwap {
+  abg_graph_desc desc{};
+  std::vector<int64_t> vp;
+  std::vector<int32_t> ui;
+  std::vector<float> wt;
+};
+int swap_sides(const abg_graph_desc* in, SideSwap* store, const abg_graph_desc** out);
 
 // ---- spmm.cu ----------------------------------------------------------------
 // Algorithm 1 propagation + Eq. 2 on device buffers. Exactly one of x_f32 /

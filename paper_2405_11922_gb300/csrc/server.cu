@@ -34,6 +34,7 @@ struct Job {
   std::vector<int32_t> labels;
   abg_result result{};
   std::string error;  // message of a failed batch, handed to the poller
+  abg::SideSwap swap; // storage behind desc when the request clusters V
   clock_t_::time_point t_submit, t_done;
 };
 
@@ -228,13 +229,22 @@ ABG_API int abg_submit(abg_server* sv, const abg_graph_desc* graph, const abg_pa
                        uint64_t* req_id) {
   using namespace abg;
   ABG_CHECK(sv && graph && params && req_id, "null argument");
-  ABG_TRY(validate_desc(graph));
-  ABG_CHECK(params->k >= 1 && params->k <= kMaxK && params->k <= graph->n_u,
-            "need 1 <= k <= min(|U|, %d)", kMaxK);
   Job* j = new Job();
-  j->desc = *graph;
+  const abg_graph_desc* gd = nullptr;
+  int st = swap_sides(graph, &j->swap, &gd);
+  if (st == ABG_OK) st = validate_desc(gd);
+  if (st == ABG_OK && !(params->k >= 1 && params->k <= kMaxK && params->k <= gd->n_u)) {
+    set_error("need 1 <= k <= min(|U|, %d)", kMaxK);
+    st = ABG_EINVAL;
+  }
+  if (st != ABG_OK) {
+    delete j;
+    return st;
+  }
+  j->desc = *gd;
+  const abg_graph_desc* graph_eff = &j->desc;
   j->params = *params;
-  j->bytes = estimate_bytes(*graph, *params);
+  j->bytes = estimate_bytes(*graph_eff, *params);
   j->t_submit = clock_t_::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

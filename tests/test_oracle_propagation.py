@@ -104,3 +104,15 @@ def test_isolated_u_keeps_restart_term():
     X = g.x_dense_f64()
     Z = tpo.propagate(L, X, 0.6, 5)
     assert np.allclose(Z[-3:], 0.4 * X[-3:])
+
+
+def test_transposed_graph_has_the_transposed_operator():
+    # clustering V runs the same method on B^T: its L is the transpose of U's L (Eq. 7)
+    g = synth.make_small(3, n_u=50, n_v=70, k=3, d_u=4, deg=4)
+    L = tpo.normalized_adjacency(tpo.adjacency(g.n_u, g.n_v, g.u_ptr, g.v_idx, g.w))
+    order = np.argsort(g.v_idx, kind="stable")
+    v_ptr = np.zeros(g.n_v + 1, dtype=np.int64)
+    np.cumsum(np.bincount(g.v_idx, minlength=g.n_v), out=v_ptr[1:])
+    rows = np.repeat(np.arange(g.n_u, dtype=np.int32), np.diff(g.u_ptr))
+    Lt = tpo.normalized_adjacency(tpo.adjacency(g.n_v, g.n_u, v_ptr, rows[order], g.w[order]))
+    assert abs(Lt - L.T).max() < 1e-15
