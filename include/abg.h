@@ -220,8 +220,15 @@ ABG_API void abg_server_destroy(abg_server* sv);
  * request's result does not depend on what it was batched with. */
 ABG_API int abg_submit(abg_server* sv, const abg_graph_desc* graph, const abg_params* params,
                        uint64_t* req_id);
-/* Wait up to timeout_us (0: do not wait; < 0: forever) for a request. ABG_OK: labels[n_u]
- * (host) and *res are filled and the id is released; ABG_PENDING (timeout 0) or
+/* Queue a request against a graph already resident on the server's device (abg_create; not a
+ * batch): re-solving with another k, alpha, seed or NCI option skips the upload and creation.
+ * The caller keeps g alive until abg_poll returns a final status for the request; several
+ * requests may share g (solves only read it). Each such request runs alone; its admission
+ * footprint is abg_solve_footprint(g, params). Labels have the graph's clustered-side size. */
+ABG_API int abg_submit_resident(abg_server* sv, abg_graph* g, const abg_params* params,
+                                uint64_t* req_id);
+/* Wait up to timeout_us (0: do not wait; < 0: forever) for a request. ABG_OK: labels (host,
+ * one per clustered node) and *res are filled and the id is released; ABG_PENDING (timeout 0) or
  * ABG_ETIMEDOUT: not finished; a negative status: the request failed (the id is released). */
 ABG_API int abg_poll(abg_server* sv, uint64_t req_id, int64_t timeout_us, int32_t* labels,
                      abg_result* res);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "abg_server_opts_default": (None, [_p]),
     "abg_server_create": (C.c_int, [_p, _p]),
     "abg_server_destroy": (None, [_p]),
+    "abg_submit_resident": (C.c_int, [_p, _p, _p, _p]),
     "abg_submit": (C.c_int, [_p, _p, _p, _p]),
     "abg_poll": (C.c_int, [_p, _u64, _i64, _p, _p]),
     "abg_server_get_stats": (C.c_int, [_p, _p]),
@@ -407,6 +408,17 @@ class Server:
         _check(st, "abg_submit")
         self._keep[rid.value] = (keep, d)
         self._n_u[rid.value] = int(g.n_v if side == ABG_SIDE_V else g.n_u)
+        return int(rid.value)
+
+    def submit_resident(self, graph: "Graph", p: abg_params) -> int:
+        """Queue a re-solve of a graph already on the device (``abg_create``); ``graph`` must
+        stay open until the request is polled to completion."""
+        rid = C.c_uint64(0)
+        st = lib().abg_submit_resident(self.handle, graph.handle, C.byref(p), C.byref(rid))
+        if st == ABG_ENOTADMITTED:
+            return -int(rid.value)
+        _check(st, "abg_submit_resident")
+        self._n_u[rid.value] = int(graph.n_u)
         return int(rid.value)
 
     def poll(self, rid: int, timeout_us: int = -1):

@@ -78,6 +78,9 @@ static_assert(kHeavyRow <= kTaskEdges && kTaskEdges % 4 == 0 && kTaskRows <= 32,
 int graph_alloc(abg_graph* g, void** p, size_t bytes, cudaStream_t s);
 // host-only validation of a graph descriptor (CSR, optional CSC, weights, attributes)
 int validate_desc(const abg_graph_desc* d);
+// Parameters of one solve on g (n_rows clustered nodes): ABG_EINVAL with a message if invalid;
+// *d_eff = the attribute width the solve uses.
+int check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d_eff);
 // A descriptor with side = ABG_SIDE_V seen as the equivalent ABG_SIDE_U descriptor (U and V
 // exchanged; a CSC the caller did not give is built into `store`, which must outlive *out).
 struct SideSwap {

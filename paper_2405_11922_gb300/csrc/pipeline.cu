@@ -19,7 +19,9 @@ struct Ev {
   }
 };
 
-int check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d_eff) {
+}  // namespace
+
+int abg::check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d_eff) {
   ABG_CHECK(g && p, "null graph or parameters");
   const int d = p->d == 0 ? g->d_u : p->d;
   ABG_CHECK(d >= 1 && d <= g->d_u, "need 1 <= d <= d_u (got d=%d, d_u=%d)", d, g->d_u);
@@ -36,6 +38,8 @@ int check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, int* d
   *d_eff = d;
   return ABG_OK;
 }
+
+namespace {
 
 // Device outputs of one batched solve.
 struct SolveOut {

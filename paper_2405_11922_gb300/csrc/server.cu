@@ -35,6 +35,8 @@ struct Job {
   abg_result result{};
   std::string error;  // message of a failed batch, handed to the poller
   abg::SideSwap swap; // storage behind desc when the request clusters V
+  abg_graph* resident = nullptr;  // solve this caller-owned graph (no upload, runs alone)
+  int64_t rows = 0;                // clustered nodes (labels)
   clock_t_::time_point t_submit, t_done;
 };
 
@@ -59,6 +61,7 @@ int64_t estimate_bytes(const abg_graph_desc& d, const abg_params& p) {
 }
 
 bool compatible(const Job& a, const Job& b) {
+  if (a.resident || b.resident) return false;  // a resident graph is solved on its own
   const abg_params &p = a.params, &q = b.params;
   return a.desc.d_u == b.desc.d_u && a.desc.x_kind == b.desc.x_kind && p.d == q.d &&
          p.alpha == q.alpha && p.gamma == q.gamma && p.t_f == q.t_f && p.t_g == q.t_g &&
@@ -118,13 +121,14 @@ void worker_main(abg_server* sv, int wid) {
       for (auto it = sv->pending.begin(); it != sv->pending.end();) {
         Job* j = *it;
         const bool fits = (int)batch.size() < sv->opts.max_batch_graphs &&
-                          (batch.empty() || rows + j->desc.n_u <= sv->opts.max_batch_rows) &&
+                          (batch.empty() || rows + j->rows <= sv->opts.max_batch_rows) &&
                           sv->inflight_bytes + bytes + j->bytes <= sv->opts.hbm_budget_bytes;
         if ((batch.empty() || compatible(*batch.front(), *j)) && fits) {
           batch.push_back(j);
           bytes += j->bytes;
-          rows += j->desc.n_u;
+          rows += j->rows;
           it = sv->pending.erase(it);
+          if (j->resident) break;
         } else {
           ++it;
         }
@@ -141,14 +145,19 @@ void worker_main(abg_server* sv, int wid) {
     for (Job* j : batch) {
       descs.push_back(j->desc);
       params.push_back(j->params);
-      rows += j->desc.n_u;
+      rows += j->rows;
     }
     abg_graph* g = nullptr;
     std::vector<int32_t> labels(rows);
     std::vector<abg_result> res(batch.size());
-    int st = abg_batch_create(descs.data(), (int32_t)descs.size(), sv->opts.device, stream, &g);
-    if (st == ABG_OK)
-      st = abg_batch_cluster(g, params.data(), stream, labels.data(), res.data());
+    int st;
+    if (batch.front()->resident) {  // one request on a caller-owned resident graph
+      st = abg_cluster(batch.front()->resident, &params[0], stream, labels.data(), res.data());
+    } else {
+      st = abg_batch_create(descs.data(), (int32_t)descs.size(), sv->opts.device, stream, &g);
+      if (st == ABG_OK)
+        st = abg_batch_cluster(g, params.data(), stream, labels.data(), res.data());
+    }
     const std::string err = st == ABG_OK ? std::string() : std::string(abg_last_error());
     if (g) abg_destroy(g);
     {
@@ -158,12 +167,12 @@ void worker_main(abg_server* sv, int wid) {
       for (size_t i = 0; i < batch.size(); ++i) {
         Job* j = batch[i];
         if (st == ABG_OK) {
-          j->labels.assign(labels.begin() + off, labels.begin() + off + j->desc.n_u);
+          j->labels.assign(labels.begin() + off, labels.begin() + off + j->rows);
           j->result = res[i];
         } else {
           j->error = err;
         }
-        off += j->desc.n_u;
+        off += j->rows;
         j->status = st;
         j->t_done = now;
         if (st == ABG_OK) sv->stats.completed += 1; else sv->stats.failed += 1;
@@ -242,9 +251,50 @@ ABG_API int abg_submit(abg_server* sv, const abg_graph_desc* graph, const abg_pa
     return st;
   }
   j->desc = *gd;
+  j->rows = gd->n_u;
   const abg_graph_desc* graph_eff = &j->desc;
   j->params = *params;
   j->bytes = estimate_bytes(*graph_eff, *params);
+  j->t_submit = clock_t_::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) {
+      delete j;
+      set_error("server is shutting down");
+      return ABG_ECANCELLED;
+    }
+    j->id = sv->next_id++;
+    *req_id = j->id;
+    sv->stats.submitted += 1;
+    if (j->bytes > sv->opts.hbm_budget_bytes) {
+      j->status = ABG_ENOTADMITTED;
+      sv->stats.rejected += 1;
+      sv->jobs[j->id] = j;
+      set_error("request needs ~%lld bytes, budget is %lld", (long long)j->bytes,
+                (long long)sv->opts.hbm_budget_bytes);
+      return ABG_ENOTADMITTED;
+    }
+    sv->jobs[j->id] = j;
+    sv->pending.push_back(j);
+  }
+  sv->cv_work.notify_one();
+  return ABG_OK;
+}
+
+ABG_API int abg_submit_resident(abg_server* sv, abg_graph* g, const abg_params* params,
+                                uint64_t* req_id) {
+  using namespace abg;
+  ABG_CHECK(sv && g && params && req_id, "null argument");
+  ABG_CHECK(g->nseg == 1, "a resident request needs a graph from abg_create, not a batch");
+  ABG_CHECK(g->device == sv->opts.device, "the graph lives on device %d, the server on %d",
+            g->device, sv->opts.device);
+  int d = 0;
+  ABG_TRY(check_params(g, params, g->n_u, &d));
+  Job* j = new Job();
+  j->resident = g;
+  j->params = *params;
+  j->rows = g->n_u;
+  j->bytes = abg_solve_footprint(g, params);
   j->t_submit = clock_t_::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

@@ -123,3 +123,35 @@ def test_concurrent_solves_of_different_widths():
     for h in handles:
         h.close()
     assert not errors, errors
+
+
+def test_resident_graph_resolves():
+    # re-solving a graph already on the device with other k / alpha / seed / NCI options: no
+    # upload, several requests on one graph at once, each equal to the plain solve
+    g = synth.make_small(80, n_u=5000, n_v=6000, k=6, d_u=16, deg=6, signal=3.0)
+    h = abg.abg_create(g)
+    ps = [abg.params(k=k, alpha=a, gamma=4, d=16, t_f=4, t_g=8, seed=s, procrustes=pr)
+          for k, a, s, pr in [(3, 0.6, 0, False), (6, 0.5, 1, False), (6, 0.6, 2, True),
+                              (4, 0.7, 3, False), (6, 0.6, 2, True)]]
+    sv = abg.Server(workers=3)
+    rids = [sv.submit_resident(h, p) for p in ps]
+    g2 = synth.make_small(81, n_u=700, n_v=900, k=3, d_u=16, deg=5)   # an uploaded request too
+    rid2 = sv.submit(g2, abg.params(k=3, alpha=0.6, gamma=4, d=16, t_f=4, t_g=8, seed=9))
+    for p, rid in zip(ps, rids):
+        st, lab, res = sv.poll(rid, 60_000_000)
+        assert st == abg.ABG_OK, abg.lib().abg_last_error().decode()
+        lab1, r1 = abg.abg_cluster(h, p)
+        assert np.array_equal(lab, lab1) and res.objective == r1.objective
+    st, lab2, _ = sv.poll(rid2, 60_000_000)
+    assert st == abg.ABG_OK and lab2.shape == (g2.n_u,)
+    s = sv.stats()
+    assert s["completed"] == 6 and s["inflight_bytes"] == 0
+    sv.close()
+    tiny = abg.Server(workers=1, hbm_budget_bytes=1 << 20)
+    assert tiny.submit_resident(h, ps[0]) < 0                  # footprint above the budget
+    b = abg.abg_batch_create([g2, g2])
+    with pytest.raises(abg.AbgError):
+        tiny.submit_resident(b, ps[0])                          # a batch is not a resident graph
+    b.close()
+    tiny.close()
+    h.close()
