@@ -508,6 +508,54 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the smaller planted workloads (1: 2,000 x 3,000, d = 500 sparse; 2: 200k x 500k, d = 128
+# reduced from 1,000 sparse attributes): solves/s and propagation rounds/s of one graph
+# ---------------------------------------------------------------------------
+
+def run_small_config(args):
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    import synth
+    if args.workload == "config1":
+        g = synth.make_config1()
+        pdict = dict(k=5, alpha=0.6, gamma=6, d=500, t_f=5, t_g=20, seed=0)
+        label = ("planted ABG |U|=2000 |V|=3000, 20,000 unit edges, binary attributes d=500 "
+                 "(no reduction), k=5, alpha=0.6, gamma=6, T_f=5, T_g=20")
+    else:
+        g = synth.make_config2()
+        pdict = dict(k=20, alpha=0.6, gamma=6, d=128, t_f=5, t_g=20, seed=0)
+        label = ("planted ABG |U|=200k |V|=500k, 5M edge draws (Zipf 2.1), TF-IDF-like sparse "
+                 "attributes d_u=1000 reduced to d=128, k=20, alpha=0.6, gamma=6, T_f=5, T_g=20")
+    p = abg.params(**pdict)
+    stream = torch.cuda.current_stream()
+    h = abg.abg_create(g, stream=stream)
+    for _ in range(args.warmup):
+        abg.abg_cluster(h, p, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        results.append(abg.abg_cluster(h, p, stream=stream)[1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    el = ev0.elapsed_time(ev1) / 1e3
+    h.close()
+    phase = [statistics.median(r.ms_phase[i] for r in results) for i in range(6)]
+    line = {"metric": "TPO solves/s and propagation rounds/s on one planted ABG",
+            "value": args.steps / el, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": label, "n_u": int(g.n_u),
+                                            "n_v": int(g.n_v), "nnz": int(g.nnz)},
+            "prop_rounds_per_s": pdict["gamma"] / (phase[1] / 1e3),
+            "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
+                                  "objective"], phase))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -516,7 +564,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["large", "batched", "serve"], default="large")
+    ap.add_argument("--workload", choices=["large", "batched", "serve", "config1", "config2"],
+                    default="large")
     ap.add_argument("--graphs", type=int, default=512, help="batched workload: number of graphs")
     ap.add_argument("--requests", type=int, default=200, help="served workload: requests")
     ap.add_argument("--pool", type=int, default=32, help="served workload: distinct graphs")
@@ -534,7 +583,8 @@ def main():
     if args.workload != "large":
         import torch
         torch.cuda.set_device(local_rank)
-        (run_batched if args.workload == "batched" else run_serve)(args)
+        {"batched": run_batched, "serve": run_serve, "config1": run_small_config,
+         "config2": run_small_config}[args.workload](args)
         return
     if world > 1:
         import torch
