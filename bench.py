@@ -126,18 +126,21 @@ def gpu_id_for_smi(local_rank: int) -> str:
         return ids[local_rank] if local_rank < len(ids) else str(local_rank)
 
 
-def propagation_bytes(g, d: int, gamma: int) -> float:
+def propagation_bytes(g, d: int, gamma: int, precision: str = "fp32") -> float:
     """Algorithmic bytes of gamma propagation rounds (both SpMMs): per round, each SpMM reads
     nnz (index + value) and one gathered d-wide row per edge, plus its row pointers and row
-    list; the first product gathers BF16 X rows, the rest FP32 Z rows; the second product also
-    reads the X restart rows (BF16) and writes Z; the first writes W."""
+    list; the first product gathers BF16 X rows, the rest Z rows; the second product also
+    reads the X restart rows (BF16) and writes Z; the first writes W. W and Z are 4-byte FP32
+    elements, or 2-byte BF16 ones (all but the final Z) with precision "bf16"."""
     nnz, n_u, n_v = g.nnz, g.n_u, g.n_v
+    e = 2 if precision == "bf16" else 4
     per_spmm_index = nnz * 8
     total = 0.0
     for r in range(gamma):
-        zin = 2 if r == 0 else 4
-        total += per_spmm_index + nnz * d * zin + n_v * (8 + 4) + n_v * d * 4     # W = L^T Z
-        total += per_spmm_index + nnz * d * 4 + n_u * (8 + 4) + n_u * d * (2 + 4)  # Z = ...
+        zin = 2 if r == 0 else e
+        zout = 4 if r == gamma - 1 else e
+        total += per_spmm_index + nnz * d * zin + n_v * (8 + 4) + n_v * d * e       # W = L^T Z
+        total += per_spmm_index + nnz * d * e + n_u * (8 + 4) + n_u * d * (2 + zout)  # Z = ...
     return total
 
 
@@ -147,7 +150,8 @@ def propagation_bytes(g, d: int, gamma: int) -> float:
 ROUND_DRAM_BYTES_FULL = 29.84e9
 
 
-def roofline_of(pbytes: float, prop_ms: float, peak: float, peak_kind: str, scale: float) -> dict:
+def roofline_of(pbytes: float, prop_ms: float, peak: float, peak_kind: str, scale: float,
+                precision: str = "fp32") -> dict:
     """Roofline of the propagation SpMMs, per round: achieved = algorithmic bytes (gathered
     rows counted once per edge) / round time; traffic = measured DRAM bytes of a round (full
     size only); traffic_gbs = the bandwidth the DRAM actually delivered."""
@@ -159,7 +163,7 @@ def roofline_of(pbytes: float, prop_ms: float, peak: float, peak_kind: str, scal
            "kernel": "propagation SpMMs per round (k_spmm_tma light tasks + heavy-row chunks, "
                      "k_spmm_reduce)",
            "per": "propagation round", "algorithmic_bytes": pbytes / gamma, "peak_kind": peak_kind}
-    if scale == 1.0:
+    if scale == 1.0 and precision == "fp32":
         out["traffic"] = ROUND_DRAM_BYTES_FULL
         out["traffic_gbs"] = ROUND_DRAM_BYTES_FULL / round_s / 1e9
         out["traffic_frac"] = out["traffic_gbs"] / peak
@@ -246,7 +250,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     g = synth.make_config3(seed=rank, scale=args.scale)
     csc = csc_of(g)
-    p = abg.params(**PARAMS)
+    p = abg.params(**PARAMS, bf16_propagation=args.precision == "bf16")
     stream = torch.cuda.current_stream()
     graph = abg.abg_create(g, device=local_rank, stream=stream, csc=csc)
     labels = torch.empty(g.n_u, dtype=torch.int32).pin_memory().numpy()
@@ -305,7 +309,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
-    pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"])
+    pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"], args.precision)
     achieved = pbytes / (prop_ms / 1e3) / 1e9
     value = world * args.steps / elapsed
     line = {
@@ -316,12 +320,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": dict(workload_of(g, args.scale), nnz=int(g.nnz),
                        parallelism=f"{world} independent solves "
                        "(one graph per rank)" if world > 1 else "single GPU",
+                       precision=args.precision,
                        l2="inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"),
         "tpo_prop_iters_per_s": PARAMS["gamma"] / (prop_ms / 1e3),
         "spmm_hbm_gbs": achieved,
         "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
                               "objective"], phase_ms)),
-        "roofline": roofline_of(pbytes, prop_ms, peak, peak_kind, args.scale),
+        "roofline": roofline_of(pbytes, prop_ms, peak, peak_kind, args.scale, args.precision),
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},
         "gpu_launches": int(launches),
@@ -573,6 +578,8 @@ def main():
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="storage of the propagation's intermediate blocks (accumulation is FP32)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -111,14 +111,26 @@ typedef struct {
  *                       from Phi^T Y = U S V^T, singular values above 1e-5 s_1)
  *   ABG_NCI_EARLY_STOP  stop after the first pass (other than the first) that
  *                       changes no label: Y and T are then a fixed point, so
- *                       the result equals that of all t_g passes. */
+ *                       the result equals that of all t_g passes.
+ * precision is ABG_PRECISION_FP32 (0, default: FP32 storage, FP32 sparse
+ * products, dense products as 3xTF32 on the tensor cores) or a combination of
+ *   ABG_BF16_PROPAGATION  Algorithm 1 stores W = L^T Z and the intermediate Z
+ *                         (rounds 1..gamma-1) in BF16 between its sparse
+ *                         products, halving the bytes each gather reads. The
+ *                         products accumulate in FP32 and Z_hat (the last
+ *                         round, Eq. 2) is FP32.
+ * reserved must be 0. */
 #define ABG_NCI_PROCRUSTES 1
 #define ABG_NCI_EARLY_STOP 2
+#define ABG_PRECISION_FP32 0
+#define ABG_BF16_PROPAGATION 2
 typedef struct {
   int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
   int32_t nci_flags;
   double alpha;
   uint64_t seed;
+  int32_t precision;
+  int32_t reserved;
 } abg_params;
 
 /* Per-solve report. objective = Eq. 8 with s(u_i,u_j) := R[i].R[j] (minimised);
@@ -249,9 +261,12 @@ ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversam
  * own dense attributes (d must equal d_u); otherwise x[n_u][ldx] (device,
  * float) is the attribute matrix of width d (e.g. abg_reduce_attributes).
  * Returns once the work on `stream` has finished (it then checks the gather
- * pipeline's bounded waits: ABG_EDEVICE if one ran out). */
+ * pipeline's bounded waits: ABG_EDEVICE if one ran out). precision is
+ * ABG_PRECISION_FP32 or ABG_BF16_PROPAGATION (storage of the intermediate
+ * blocks, as in abg_params). */
 ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32_t d,
-                          double alpha, int32_t gamma, float* zhat, int64_t ldz, void* stream);
+                          double alpha, int32_t gamma, int32_t precision, float* zhat,
+                          int64_t ldz, void* stream);
 
 /* Algorithm 1: q_out[d][d] (device, double) = the orthogonal factor of the QR
  * of G ~ N(0,1)^{d x d} drawn on ABG_STREAM_G, with diag(R_qr) > 0. */

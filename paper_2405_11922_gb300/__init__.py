@@ -38,7 +38,7 @@ class abg_graph_desc(C.Structure):
 class abg_params(C.Structure):
     _fields_ = [("k", _i32), ("gamma", _i32), ("d", _i32), ("t_f", _i32), ("t_g", _i32),
                 ("oversample", _i32), ("power_iters", _i32), ("nci_flags", _i32),
-                ("alpha", _f64), ("seed", _u64)]
+                ("alpha", _f64), ("seed", _u64), ("precision", _i32), ("reserved", _i32)]
 
 
 class abg_result(C.Structure):
@@ -91,7 +91,7 @@ SIGNATURES = {
     "abg_poll": (C.c_int, [_p, _u64, _i64, _p, _p]),
     "abg_server_get_stats": (C.c_int, [_p, _p]),
     "abg_reduce_attributes": (C.c_int, [_p, _i32, _i32, _i32, _u64, _p, _i64, _p]),
-    "abg_propagate": (C.c_int, [_p, _p, _i64, _i32, _f64, _i32, _p, _i64, _p]),
+    "abg_propagate": (C.c_int, [_p, _p, _i64, _i32, _f64, _i32, _i32, _p, _i64, _p]),
     "abg_orthogonal_matrix": (C.c_int, [_u64, _i32, _p, _p]),
     "abg_random_features": (C.c_int, [_p, _i64, _i32, _i64, _u64, _p, _i64, _p, _p]),
     "abg_seed_factors": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _i32, _u64, _p, _i64, _p,
@@ -160,16 +160,19 @@ def _ld(t) -> int:
 
 ABG_NCI_PROCRUSTES = 1
 ABG_NCI_EARLY_STOP = 2
+ABG_PRECISION_FP32 = 0
+ABG_BF16_PROPAGATION = 2
 
 
 def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5, t_g: int = 20,
            oversample: int = 10, power_iters: int = 4, seed: int = 0, procrustes: bool = False,
-           early_stop: bool = False) -> abg_params:
+           early_stop: bool = False, bf16_propagation: bool = False) -> abg_params:
     p = abg_params()
     lib().abg_params_default(C.byref(p))
     p.k, p.alpha, p.gamma, p.d, p.t_f, p.t_g = k, alpha, gamma, d, t_f, t_g
     p.oversample, p.power_iters, p.seed = oversample, power_iters, seed
     p.nci_flags = (ABG_NCI_PROCRUSTES if procrustes else 0) | (ABG_NCI_EARLY_STOP if early_stop else 0)
+    p.precision = ABG_BF16_PROPAGATION if bf16_propagation else ABG_PRECISION_FP32
     return p
 
 
@@ -322,9 +325,11 @@ def abg_reduce_attributes(graph: Graph, d: int, x_out, oversample=10, power_iter
     return x_out
 
 
-def abg_propagate(graph: Graph, x, d: int, alpha: float, gamma: int, zhat, stream=None):
+def abg_propagate(graph: Graph, x, d: int, alpha: float, gamma: int, zhat, stream=None,
+                  bf16_propagation: bool = False):
     _check(lib().abg_propagate(graph.handle, _ptr(x), _ld(x) if x is not None else 0, d, alpha,
-                               gamma, _ptr(zhat), _ld(zhat), _stream(stream)), "abg_propagate")
+                               gamma, ABG_BF16_PROPAGATION if bf16_propagation else 0, _ptr(zhat),
+                               _ld(zhat), _stream(stream)), "abg_propagate")
     return zhat
 
 

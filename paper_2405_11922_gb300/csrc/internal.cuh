@@ -97,8 +97,11 @@ int swap_sides(const abg_graph_desc* in, SideSwap* store, const abg_graph_desc**
 // Reads (and clears) the graph's wait flag after the stream's work: ABG_EDEVICE when a
 // bounded wait inside a kernel ran out. Synchronises s.
 int check_wait_flag(const abg_graph* g, cudaStream_t s);
+// bf16_rounds: W and the intermediate Z are stored in BF16 between the SpMMs (each gather
+// still accumulates in FP32); the final Z-hat is FP32 either way.
 int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf16, int64_t ldx,
-              int d, double alpha, int gamma, float* zhat, int64_t ldz, cudaStream_t s);
+              int d, double alpha, int gamma, float* zhat, int64_t ldz, cudaStream_t s,
+              bool bf16_rounds = false);
 // C[rows][ldc] = A_csr (rows x K) * B[K][ldb] (width n, plain sum per row).
 int spmm_plain(const int64_t* ptr, const int32_t* col, const float* val, int64_t rows,
                const float* B, int64_t ldb, int n, float* C, int64_t ldc, cudaStream_t s);

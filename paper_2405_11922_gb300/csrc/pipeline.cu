@@ -35,6 +35,8 @@ int abg::check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, i
             "attribute reduction needs d + oversample <= 1024");
   ABG_CHECK((p->nci_flags & ~(ABG_NCI_PROCRUSTES | ABG_NCI_EARLY_STOP)) == 0,
             "unknown nci_flags %d", p->nci_flags);
+  ABG_CHECK((p->precision & ~ABG_BF16_PROPAGATION) == 0, "unknown precision %d", p->precision);
+  ABG_CHECK(p->reserved == 0, "abg_params.reserved must be 0");
   *d_eff = d;
   return ABG_OK;
 }
@@ -225,7 +227,8 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   float* zhat;
   ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
   if (ev) ABG_CUDA(cudaEventRecord(ev[1], s));
-  ABG_TRY(propagate(g, xf, xb, ldx, d, p.alpha, p.gamma, zhat, ldz, s));
+  ABG_TRY(propagate(g, xf, xb, ldx, d, p.alpha, p.gamma, zhat, ldz, s,
+                    (p.precision & ABG_BF16_PROPAGATION) != 0));
   if (ev) ABG_CUDA(cudaEventRecord(ev[2], s));
   double* q;
   float* qt;
@@ -287,9 +290,9 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     ABG_CHECK(di == d && ps[i].alpha == ps[0].alpha && ps[i].gamma == ps[0].gamma &&
                   ps[i].t_f == ps[0].t_f && ps[i].t_g == ps[0].t_g &&
                   ps[i].oversample == ps[0].oversample && ps[i].power_iters == ps[0].power_iters &&
-                  ps[i].nci_flags == ps[0].nci_flags,
+                  ps[i].nci_flags == ps[0].nci_flags && ps[i].precision == ps[0].precision,
               "batched solves need the same d, alpha, gamma, t_f, t_g, oversample, power_iters, "
-              "nci_flags");
+              "nci_flags, precision");
   }
   ABG_CUDA(cudaSetDevice(g->device));
   const int nseg = g->nseg;
@@ -377,6 +380,8 @@ ABG_API void abg_params_default(abg_params* p) {
   p->nci_flags = 0;
   p->alpha = 0.6;
   p->seed = 0;
+  p->precision = ABG_PRECISION_FP32;
+  p->reserved = 0;
 }
 
 ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
@@ -388,7 +393,10 @@ ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
   const int64_t ll = round_up(l, 4);
   int64_t b = 0;
   b += 4 * n * ld;                       // Z_hat
-  b += 4 * g->n_v * ld;                  // W
+  if (p->precision & ABG_BF16_PROPAGATION)  // W and the intermediate Z in BF16
+    b += 2 * round_up(d, 8) * (g->n_v + (p->gamma > 1 ? n : 0));
+  else
+    b += 4 * g->n_v * ld;                // W
   b += 4 * n * ldr;                      // R
   b += 4 * n * ll * 2;                   // randomized SVD blocks
   b += 4 * n * kk * 4;                   // Phi (x2), P, spare
@@ -441,12 +449,16 @@ ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversam
 }
 
 ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32_t d, double alpha,
-                          int32_t gamma, float* zhat, int64_t ldz, void* stream) {
+                          int32_t gamma, int32_t precision, float* zhat, int64_t ldz,
+                          void* stream) {
   ABG_CHECK(g && zhat, "null argument");
+  ABG_CHECK(precision == ABG_PRECISION_FP32 || precision == ABG_BF16_PROPAGATION,
+            "unknown precision %d", precision);
+  const bool bf16 = precision == ABG_BF16_PROPAGATION;
   ABG_CUDA(cudaSetDevice(g->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (x) {
-    ABG_TRY(propagate(g, x, nullptr, ldx, d, alpha, gamma, zhat, ldz, s));
+    ABG_TRY(propagate(g, x, nullptr, ldx, d, alpha, gamma, zhat, ldz, s, bf16));
     return check_wait_flag(g, s);
   }
   ABG_CHECK(d == g->d_u, "x = NULL needs d == d_u");
@@ -458,7 +470,7 @@ ABG_API int abg_propagate(const abg_graph* g, const float* x, int64_t ldx, int32
   int64_t lx;
   std::vector<uint64_t> seeds(g->nseg, 0);
   ABG_TRY(prepare_attributes(g, rs, d, 0, 0, seeds, scr, s, &xf, &xb, &lx, nullptr));
-  ABG_TRY(propagate(g, xf, xb, lx, d, alpha, gamma, zhat, ldz, s));
+  ABG_TRY(propagate(g, xf, xb, lx, d, alpha, gamma, zhat, ldz, s, bf16));
   return check_wait_flag(g, s);
 }
 

@@ -66,7 +66,7 @@ bool compatible(const Job& a, const Job& b) {
   return a.desc.d_u == b.desc.d_u && a.desc.x_kind == b.desc.x_kind && p.d == q.d &&
          p.alpha == q.alpha && p.gamma == q.gamma && p.t_f == q.t_f && p.t_g == q.t_g &&
          p.oversample == q.oversample && p.power_iters == q.power_iters &&
-         p.nci_flags == q.nci_flags;
+         p.nci_flags == q.nci_flags && p.precision == q.precision;
 }
 
 }  // namespace

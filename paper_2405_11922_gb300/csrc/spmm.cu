@@ -25,6 +25,7 @@ struct EpiParams {
   int x_bf16;
   int64_t ldx;
   int d;             // row width: components at or beyond d are treated as 0 and written as 0
+  int out_bf16;      // C holds BF16 values (rounded to nearest even), row stride ldc elements
 };
 
 template <class T>
@@ -168,7 +169,17 @@ __device__ __forceinline__ void epilogue_core(int64_t row, const float4 (&acc_in
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     int ch = lig + G * v;
-    if (ch < nchunk) st_f4(C + row * ldc + 4 * ch, out[v]);
+    if (ch >= nchunk) continue;
+    if (ep.out_bf16) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(out[v].x, out[v].y);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(out[v].z, out[v].w);
+      uint2 u;
+      u.x = *reinterpret_cast<const uint32_t*>(&lo);
+      u.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(C) + row * ldc + 4 * ch) = u;
+    } else {
+      st_f4(C + row * ldc + 4 * ch, out[v]);
+    }
   }
 }
 
@@ -906,7 +917,8 @@ static int run_scale_rows(int64_t n_rows, float* C, int64_t ldc, int nchunk, con
 }
 
 int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf16, int64_t ldx,
-              int d, double alpha, int gamma, float* zhat, int64_t ldz, cudaStream_t s) {
+              int d, double alpha, int gamma, float* zhat, int64_t ldz, cudaStream_t s,
+              bool bf16_rounds) {
   ABG_CHECK(d >= 1 && d <= kMaxD, "propagate: need 1 <= d <= %d", kMaxD);
   ABG_CHECK(gamma >= 0, "propagate: gamma < 0");
   ABG_CHECK(alpha >= 0.0 && alpha < 1.0, "propagate: need 0 <= alpha < 1");
@@ -922,34 +934,53 @@ int propagate(const abg_graph* g, const float* x_f32, const __nv_bfloat16* x_bf1
     return run_scale_rows(g->n_u, zhat, ldz, nchunk, ep, s);
   }
   Scratch scr(s);
-  const int64_t ldw = round_up(d, 4);
-  float* W;
-  ABG_TRY(scr.get(&W, (size_t)g->n_v * ldw));
+  const int64_t ldw = round_up(d, 4);   // FP32 rows (and the heavy-row partials)
+  const int64_t ldh = round_up(d, 8);   // BF16 rows (16-byte aligned)
+  float* W = nullptr;
+  __nv_bfloat16 *Wb = nullptr, *Zb = nullptr;
+  if (bf16_rounds) {  // W and the intermediate Z stored in BF16, accumulated in FP32
+    ABG_TRY(scr.get(&Wb, (size_t)g->n_v * ldh));
+    if (gamma > 1) ABG_TRY(scr.get(&Zb, (size_t)g->n_u * ldh));
+  } else {
+    ABG_TRY(scr.get(&W, (size_t)g->n_v * ldw));
+  }
   int64_t nparts = std::max<int64_t>(1, std::max(g->sched_u.n_chunks, g->sched_v.n_chunks));
   float* part;
   ABG_TRY(scr.get(&part, (size_t)nparts * ldw));
+  float* Wout = bf16_rounds ? reinterpret_cast<float*>(Wb) : W;
+  const int64_t ldwo = bf16_rounds ? ldh : ldw;
   for (int it = 0; it < gamma; ++it) {
     // W = L^T Z   (Z_0 = (1-a) X gathered straight from the attributes)
-    if (it == 0) {
-      EpiParams ep{0, (float)(1.0 - alpha), 0.f, 0.f, nullptr, 0, 0, d};
-      if (x_bf16)
-        ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col,
-                                             g->v_val, x_bf16, ldx, g->n_u, W, ldw, nchunk, ep,
-                                             part, ldw, g->wait_err, s));
-      else
-        ABG_TRY(dispatch_spmm<float>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val,
-                                     x_f32, ldx, g->n_u, W, ldw, nchunk, ep, part, ldw,
-                                     g->wait_err, s));
-    } else {
-      EpiParams ep{0, 1.f, 0.f, 0.f, nullptr, 0, 0, d};
+    EpiParams ev{0, it == 0 ? (float)(1.0 - alpha) : 1.f, 0.f, 0.f, nullptr, 0, 0, d,
+                 bf16_rounds ? 1 : 0};
+    if (it == 0 && x_bf16)
+      ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val,
+                                           x_bf16, ldx, g->n_u, Wout, ldwo, nchunk, ev, part, ldw,
+                                           g->wait_err, s));
+    else if (it == 0)
+      ABG_TRY(dispatch_spmm<float>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val, x_f32,
+                                   ldx, g->n_u, Wout, ldwo, nchunk, ev, part, ldw, g->wait_err, s));
+    else if (bf16_rounds)
+      ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val,
+                                           Zb, ldh, g->n_u, Wout, ldwo, nchunk, ev, part, ldw,
+                                           g->wait_err, s));
+    else
       ABG_TRY(dispatch_spmm<float>(&g->sched_v, nullptr, 0, g->v_ptr, g->v_col, g->v_val, zhat,
-                                   ldz, g->n_u, W, ldw, nchunk, ep, part, ldw, g->wait_err, s));
-    }
-    // Z = (1-a) X + a L W   (+ Eq. 2 on the last round)
-    EpiParams ep = ep_restart;
-    ep.mode = (it == gamma - 1) ? 2 : 1;
-    ABG_TRY(dispatch_spmm<float>(&g->sched_u, nullptr, 0, g->u_ptr, g->u_col, g->u_val, W, ldw,
-                                 g->n_v, zhat, ldz, nchunk, ep, part, ldw, g->wait_err, s));
+                                   ldz, g->n_u, Wout, ldwo, nchunk, ev, part, ldw, g->wait_err, s));
+    // Z = (1-a) X + a L W   (+ Eq. 2 on the last round, always written in FP32)
+    const bool last = it == gamma - 1;
+    EpiParams eu = ep_restart;
+    eu.mode = last ? 2 : 1;
+    eu.out_bf16 = bf16_rounds && !last;
+    float* Zout = eu.out_bf16 ? reinterpret_cast<float*>(Zb) : zhat;
+    const int64_t ldzo = eu.out_bf16 ? ldh : ldz;
+    if (bf16_rounds)
+      ABG_TRY(dispatch_spmm<__nv_bfloat16>(&g->sched_u, nullptr, 0, g->u_ptr, g->u_col, g->u_val,
+                                           Wb, ldh, g->n_v, Zout, ldzo, nchunk, eu, part, ldw,
+                                           g->wait_err, s));
+    else
+      ABG_TRY(dispatch_spmm<float>(&g->sched_u, nullptr, 0, g->u_ptr, g->u_col, g->u_val, W, ldw,
+                                   g->n_v, Zout, ldzo, nchunk, eu, part, ldw, g->wait_err, s));
   }
   return ABG_OK;
 }
