@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Benchmark of the TPO hot path on one GB300 (and N independent replicas under torchrun).
 
-A step is one full solve (Algorithms 1-3 and the objective) of the large planted-partition
+A step is one full solve (Algorithms 1-3, T of Algorithm 3 as the Procrustes factor of Phi^T Y,
+and the objective) of the large planted-partition
 workload: |U| = 2,000,000, |V| = 5,000,000, 50M edge draws (Chung-Lu exponent 2.2 on both
 sides, 60/40 mixing), dense Gaussian-mixture attributes d = 128 stored as BF16, k = 100,
 alpha = 0.9, gamma = 10, T_f = 5, T_g = 20. Inputs are synthetic (seeded generator) and far
@@ -47,6 +48,9 @@ def workload_of(g, scale: float) -> dict:
 
 PARAMS = dict(k=100, alpha=0.9, gamma=10, d=128, t_f=5, t_g=20, seed=0)
 ORACLE_SCALES = (0.01, 0.02)   # oracle sample sizes (fraction of the full workload)
+NCI_NAMES = {"procrustes": "Algorithm 3 with T = orthogonal Procrustes factor of Phi^T Y "
+                           "(T T^T = I of Eq. 20)",
+             "printed": "Algorithm 3 with T = Phi^T Y"}
 
 
 def measured_peak():
@@ -196,7 +200,27 @@ class PinnedGraph:
         self.h2d_bytes = sum(int(a.nbytes) for a in arr if a is not None)
 
 
-def oracle_sample(seed: int = 0) -> dict:
+def nmi(a, b) -> float:
+    """Normalised mutual information (geometric mean normalisation) of two labelings."""
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    ka, kb = int(a.max()) + 1, int(b.max()) + 1
+    p = np.bincount(a * kb + b, minlength=ka * kb).reshape(ka, kb) / a.size
+    pa, pb = p.sum(1), p.sum(0)
+    nz = p > 0
+    mi = float((p[nz] * np.log(p[nz] / np.outer(pa, pb)[nz])).sum())
+    ha = -float((pa[pa > 0] * np.log(pa[pa > 0])).sum())
+    hb = -float((pb[pb > 0] * np.log(pb[pb > 0])).sum())
+    return mi / np.sqrt(ha * hb) if ha > 0 and hb > 0 else 0.0
+
+
+def quality_of(g, labels, res) -> dict:
+    return {"clusters_nonempty": int(np.unique(labels).size),
+            "nmi_vs_planted": round(nmi(g.truth, labels), 4) if g.truth is not None else None,
+            "objective_eq8": res.objective}
+
+
+def oracle_sample(seed: int = 0, procrustes: bool = True) -> dict:
     """Time the FP64 oracle on two small instances of the workload generator and extrapolate
     linearly to the full size (every phase is linear in |U| and |E| at fixed d and k)."""
     import synth
@@ -205,7 +229,7 @@ def oracle_sample(seed: int = 0) -> dict:
     for sc in ORACLE_SCALES:
         g = synth.make_config3(seed=seed, scale=sc)
         t0 = time.perf_counter()
-        tpo.tpo(g, **PARAMS)
+        tpo.tpo(g, **PARAMS, procrustes=procrustes)
         times.append(time.perf_counter() - t0)
     (s0, s1), (t0, t1) = ORACLE_SCALES, times
     slope = (t1 - t0) / (s1 - s0)
@@ -222,7 +246,7 @@ def run_reference(args, rank: int):
         return
     vals = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(seed=0)
+        r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
         if i >= args.warmup:
             vals.append(1.0 / r["seconds_full_est"])
     v = statistics.median(vals)
@@ -230,7 +254,7 @@ def run_reference(args, rank: int):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism="cpu oracle"),
+            "config": dict(WORKLOAD, nci=NCI_NAMES[args.nci], parallelism="cpu oracle"),
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -250,7 +274,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
     g = synth.make_config3(seed=rank, scale=args.scale)
     csc = csc_of(g)
-    p = abg.params(**PARAMS, bf16_propagation=args.precision == "bf16")
+    p = abg.params(**PARAMS, procrustes=args.nci == "procrustes",
+                   bf16_propagation=args.precision == "bf16")
     stream = torch.cuda.current_stream()
     graph = abg.abg_create(g, device=local_rank, stream=stream, csc=csc)
     labels = torch.empty(g.n_u, dtype=torch.int32).pin_memory().numpy()
@@ -320,7 +345,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": dict(workload_of(g, args.scale), nnz=int(g.nnz),
                        parallelism=f"{world} independent solves "
                        "(one graph per rank)" if world > 1 else "single GPU",
-                       precision=args.precision,
+                       precision=args.precision, nci=NCI_NAMES[args.nci],
                        l2="inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"),
         "tpo_prop_iters_per_s": PARAMS["gamma"] / (prop_ms / 1e3),
         "spmm_hbm_gbs": achieved,
@@ -330,10 +355,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},
         "gpu_launches": int(launches),
+        "quality": quality_of(g, labels, results[-1]),
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
     if world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(seed=0)
+        r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
         line["cpu_baseline"] = {"value": 1.0 / r["seconds_full_est"], "unit": "solves/s",
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
     print(json.dumps(line), flush=True)
@@ -578,6 +604,9 @@ def main():
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--nci", choices=["procrustes", "printed"], default="procrustes",
+                    help="T update of Algorithm 3 (the printed T = Phi^T Y collapses this "
+                         "workload into one cluster)")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
                     help="storage of the propagation's intermediate blocks (accumulation is FP32)")
     args = ap.parse_args()

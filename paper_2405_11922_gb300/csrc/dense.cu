@@ -791,7 +791,9 @@ int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ld
   double* S;
   ABG_TRY(scr.get(&S, (size_t)nseg * ((size_t)kmax * kmax + kmax)));
   double *M = nullptr, *W = nullptr, *evals = nullptr, *evecs = nullptr;
+  float* warm = nullptr;  // right singular vectors of the last pass's Phi^T Y
   if (procrustes) {
+    ABG_TRY(scr.get(&warm, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&M, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&W, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&evals, (size_t)nseg * kmax));
@@ -828,7 +830,9 @@ int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ld
     k_nci_finalize<<<g, 256, 0, s>>>(ss.k, kmax, S, kp, T, t_out, counters + 2 * nseg, M);
     note_launch();
     if (procrustes) {
-      ABG_TRY(svd_right(nseg, kmax, ss.k, kmax, M, evals, evecs, s));
+      // consecutive passes move few labels, so Phi^T Y changes little: the Jacobi sweeps start
+      // from the previous pass's rotations
+      ABG_TRY(svd_right(nseg, kmax, ss.k, kmax, M, evals, evecs, s, warm, t > 0));
       k_polar_w<<<g, 256, 0, s>>>(ss.k, kmax, M, evals, evecs, W);
       note_launch();
       k_polar_t<<<g, 256, 0, s>>>(ss.k, kmax, W, evecs, kp, T, t_out);

@@ -202,9 +202,10 @@ int objective(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int
 // ---- linalg.cu --------------------------------------------------------------
 // Right singular vectors and squared singular values (descending) of Bt_s (m x l_s, FP64, row
 // stride lmax inside an m*lmax slab): FP32 one-sided Jacobi, results FP64 (l_s x l_s slabs of
-// stride lmax).
+// stride lmax). warm (nseg slabs of lmax*lmax floats, optional): the rotations are stored
+// there on exit, and with warm_valid the sweeps start from the ones stored by the last call.
 int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
-              double* evecs, cudaStream_t s);
+              double* evecs, cudaStream_t s, float* warm = nullptr, bool warm_valid = false);
 // Gaussian matrix (rows x cols, row stride ld) of each segment from (seeds[s], stream id); the
 // segment's block sits at out + s*oseg; columns >= cols_s (segcols) are set to 0.
 int gaussian_f64(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols, double* out,

@@ -402,13 +402,17 @@ int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy
 // the error of sigma_j near 1e-7 sigma_1, the accuracy of the FP32 products
 // that formed Bt_s, at a fraction of the cost of FP64 on this GPU.
 // evals_s (sigma^2, descending) and evecs_s (columns, row stride lmax) are written.
+// Warm start (warm != null, shared-memory case): with warm_in set, the sweeps start from
+// W = Bt_s V0 and V = V0 for the orthogonal V0 stored there (the rotations of an earlier,
+// nearby matrix, so few sweeps remain); on exit the accumulated V is stored back.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restrict__ segl,
                                                        int lmax, const double* __restrict__ Btall,
                                                        float* __restrict__ Wg_all,
                                                        float* __restrict__ Vg_all, int in_smem,
                                                        int max_sweeps, double* __restrict__ evals,
-                                                       double* __restrict__ evecs) {
+                                                       double* __restrict__ evecs,
+                                                       float* __restrict__ warm, int warm_in) {
   extern __shared__ float sv_smem[];
   __shared__ int s_rot;
   const int sg = blockIdx.x;
@@ -419,52 +423,86 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
   float* V = in_smem ? sv_smem + (int64_t)m * l : Vg_all + (int64_t)sg * lmax * lmax;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  for (int64_t q = tid; q < (int64_t)m * l; q += nt) {
-    const int j = (int)(q / m), r = (int)(q % m);
-    W[q] = (float)Bt[(int64_t)r * lmax + j];
+  float* V0 = warm ? warm + (int64_t)sg * lmax * lmax : nullptr;
+  if (V0 && warm_in) {
+    // the stored columns, renormalised (FP32 rotations let their norms drift over many calls)
+    for (int j = warp; j < l; j += nw) {
+      const float* vj = V0 + (int64_t)j * l;
+      float acc = 0.f;
+      for (int r = lane; r < l; r += 32) acc = fmaf(vj[r], vj[r], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const float inv = acc > 0.f ? rsqrtf(acc) : 0.f;
+      for (int r = lane; r < l; r += 32) V[(int64_t)j * l + r] = vj[r] * inv;
+    }
+    __syncthreads();
+    for (int64_t q = tid; q < (int64_t)m * l; q += nt) {  // W = Bt V0
+      const int j = (int)(q / m), r = (int)(q % m);
+      const double* br = Bt + (int64_t)r * lmax;
+      const float* vj = V + (int64_t)j * l;
+      float acc = 0.f;
+      for (int p = 0; p < l; ++p) acc = fmaf((float)br[p], vj[p], acc);
+      W[q] = acc;
+    }
+  } else {
+    for (int64_t q = tid; q < (int64_t)m * l; q += nt) {
+      const int j = (int)(q / m), r = (int)(q % m);
+      W[q] = (float)Bt[(int64_t)r * lmax + j];
+    }
+    for (int64_t q = tid; q < (int64_t)l * l; q += nt) V[q] = (q / l) == (q % l) ? 1.f : 0.f;
   }
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt) V[q] = (q / l) == (q % l) ? 1.f : 0.f;
   __syncthreads();
   const int mp = (l + 1) & ~1;  // even player count; index l is a bye when l is odd
   const int P = mp / 2;
+  // G lanes per column pair, so that one pass of the CTA's groups covers a step's P pairs
+  // where it can (G >= 8 keeps the column loops a few elements deep per lane)
+  const int G = P <= nw ? 32 : (P <= 2 * nw ? 16 : 8);
+  const int gpw = 32 / G, gi = lane / G, gl = lane % G;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     int rotated = 0;
     for (int step = 0; step < mp - 1; ++step) {
-      for (int i = warp; i < P; i += nw) {
+      // i0 is uniform over the warp, so every lane runs the same trips and the shuffles below
+      // see all 32 lanes; groups without a pair carry zeros and rotate nothing
+      for (int i0 = warp * gpw; i0 < P; i0 += nw * gpw) {
+        const int i = i0 + gi;
         auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (mp - 1)) + 1; };
-        const int a = player(i), b = player(mp - 1 - i);
-        const int pc = min(a, b), qc = max(a, b);
-        if (qc >= l) continue;
+        int pc = 0, qc = l;
+        if (i < P) {
+          const int a = player(i), b = player(mp - 1 - i);
+          pc = min(a, b);
+          qc = max(a, b);
+        }
+        const bool valid = qc < l;
         float* wp = W + (int64_t)pc * m;
-        float* wq = W + (int64_t)qc * m;
+        float* wq = W + (int64_t)(valid ? qc : pc) * m;
         float al = 0.f, be = 0.f, ga = 0.f;
-        for (int r = lane; r < m; r += 32) {
-          const float x = wp[r], y = wq[r];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
+        if (valid)
+          for (int r = gl; r < m; r += G) {
+            const float x = wp[r], y = wq[r];
+            al = fmaf(x, x, al);
+            be = fmaf(y, y, be);
+            ga = fmaf(x, y, ga);
+          }
+        for (int o = G / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o, G);
+          be += __shfl_xor_sync(0xffffffffu, be, o, G);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o, G);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (!(fabsf(ga) > 1e-6f * sqrtf(al * be))) continue;  // uniform over the warp
+        if (!valid || !(fabsf(ga) > 1e-6f * sqrtf(al * be))) continue;  // uniform over the group
         const float zeta = (be - al) / (2.f * ga);
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float c = rsqrtf(fmaf(t, t, 1.f));
         const float sn = c * t;
-        for (int r = lane; r < m; r += 32) {
+        for (int r = gl; r < m; r += G) {
           const float x = wp[r], y = wq[r];
           wp[r] = c * x - sn * y;
           wq[r] = sn * x + c * y;
         }
         float* vp = V + (int64_t)pc * l;
         float* vq = V + (int64_t)qc * l;
-        for (int r = lane; r < l; r += 32) {
+        for (int r = gl; r < l; r += G) {
           const float x = vp[r], y = vq[r];
           vp[r] = c * x - sn * y;
           vq[r] = sn * x + c * y;
@@ -473,6 +511,7 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
       }
       __syncthreads();
     }
+    rotated = __any_sync(0xffffffffu, rotated);
     if (rotated && lane == 0) atomicOr(&s_rot, 1);
     __syncthreads();
     const bool done = s_rot == 0;
@@ -503,10 +542,12 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
     ev[rank] = (double)li;
     for (int k = 0; k < l; ++k) ec[(int64_t)k * lmax + rank] = (double)V[(int64_t)i * l + k];
   }
+  if (V0)
+    for (int64_t q = tid; q < (int64_t)l * l; q += nt) V0[q] = V[q];
 }
 
 int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
-              double* evecs, cudaStream_t s) {
+              double* evecs, cudaStream_t s, float* warm, bool warm_valid) {
   ABG_CHECK(lmax <= kMaxRsvdBlock, "svd: block width above %d", kMaxRsvdBlock);
   Scratch scr(s);
   const size_t smem = sizeof(float) * ((size_t)m * lmax + (size_t)lmax * lmax);
@@ -518,8 +559,9 @@ int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, doub
   } else {
     ABG_TRY(raise_smem_limit((const void*)k_svd_onesided, smem));
   }
-  k_svd_onesided<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(m, segl, lmax, Bt, W, V, in_smem,
-                                                                   40, evals, evecs);
+  if (!in_smem) warm = nullptr;  // the warm start keeps V in shared memory
+  k_svd_onesided<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(
+      m, segl, lmax, Bt, W, V, in_smem, 40, evals, evecs, warm, warm && warm_valid ? 1 : 0);
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
