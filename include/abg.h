@@ -114,6 +114,17 @@ typedef struct {
  *                       the result equals that of all t_g passes.
  * precision is ABG_PRECISION_FP32 (0, default: FP32 storage, FP32 sparse
  * products, dense products as 3xTF32 on the tensor cores) or a combination of
+ *   ABG_BF16_CONTRACT     the dense contractions with the random-feature matrix
+ *                         R (Algorithm 2: the randomized SVD's R Omega, R^T Q,
+ *                         R Q'; Eqs. 16-17: R^T Phi, R H) and, with d < d_u
+ *                         and BF16 attributes, those of the attribute SVD
+ *                         (Section 3.2.1) run on the tensor cores with BF16
+ *                         operands (R kept as a BF16 copy, the small operand
+ *                         rounded to BF16) and FP32 accumulation. Gram
+ *                         matrices, Cholesky-QR, the NCI scores and the
+ *                         objective stay FP32 / FP64. Applies where the
+ *                         BF16 kernels take the shape (2d <= 256 for the
+ *                         R^T products); elsewhere the FP32 path runs.
  *   ABG_BF16_PROPAGATION  Algorithm 1 stores W = L^T Z and the intermediate Z
  *                         (rounds 1..gamma-1) in BF16 between its sparse
  *                         products, halving the bytes each gather reads. The
@@ -123,6 +134,7 @@ typedef struct {
 #define ABG_NCI_PROCRUSTES 1
 #define ABG_NCI_EARLY_STOP 2
 #define ABG_PRECISION_FP32 0
+#define ABG_BF16_CONTRACT 1
 #define ABG_BF16_PROPAGATION 2
 typedef struct {
   int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
@@ -281,17 +293,20 @@ ABG_API int abg_random_features(const float* zhat, int64_t n, int32_t d, int64_t
 
 /* Algorithm 2 seeding (Eq. 18): truncated randomized SVD of r[n][m] (stream
  * ABG_STREAM_OMEGA_R), phi_out[n][ldphi] = max(Gamma, 0), h_out[m][ldh] =
- * max(Psi Sigma, 0), sigma_out[k] (device, double, may be NULL). */
+ * max(Psi Sigma, 0), sigma_out[k] (device, double, may be NULL). precision:
+ * ABG_PRECISION_FP32 or ABG_BF16_CONTRACT (the products with r in BF16, as in
+ * abg_params). */
 ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k,
                              int32_t oversample, int32_t power_iters, uint64_t seed,
                              float* phi_out, int64_t ldphi, float* h_out, int64_t ldh,
-                             double* sigma_out, void* stream);
+                             double* sigma_out, int32_t precision, void* stream);
 
 /* Algorithm 2 loop: t_f times H by Eq. 16 then Phi by Eq. 17, in place on
  * phi[n][ldphi] and h[m][ldh] (max(numerator, 0); a non-positive denominator
- * sets the entry to 0). */
+ * sets the entry to 0). precision as for abg_seed_factors. */
 ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k, int32_t t_f,
-                     float* phi, int64_t ldphi, float* h, int64_t ldh, void* stream);
+                     float* phi, int64_t ldphi, float* h, int64_t ldh, int32_t precision,
+                     void* stream);
 
 /* Algorithm 3: T = I; t_g times l* = argmax_l Phi[i].T[:, l] (ties -> lowest
  * l), Y by Eqs. 22-23, T <- Phi^T Y (or its Procrustes factor, see

@@ -95,8 +95,8 @@ SIGNATURES = {
     "abg_orthogonal_matrix": (C.c_int, [_u64, _i32, _p, _p]),
     "abg_random_features": (C.c_int, [_p, _i64, _i32, _i64, _u64, _p, _i64, _p, _p]),
     "abg_seed_factors": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _i32, _u64, _p, _i64, _p,
-                                   _i64, _p, _p]),
-    "abg_onmf": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _i64, _p, _i64, _p]),
+                                   _i64, _p, _i32, _p]),
+    "abg_onmf": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _i64, _p, _i64, _i32, _p]),
     "abg_nci": (C.c_int, [_p, _i64, _i32, _i64, _i32, _i32, _p, _p, _p, _p, _p, _p]),
     "abg_objective": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
     "abg_objective_noalloc": (C.c_int, [_p, _i64, _i32, _i64, _p, _i32, _p, _p]),
@@ -161,18 +161,21 @@ def _ld(t) -> int:
 ABG_NCI_PROCRUSTES = 1
 ABG_NCI_EARLY_STOP = 2
 ABG_PRECISION_FP32 = 0
+ABG_BF16_CONTRACT = 1
 ABG_BF16_PROPAGATION = 2
 
 
 def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5, t_g: int = 20,
            oversample: int = 10, power_iters: int = 4, seed: int = 0, procrustes: bool = False,
-           early_stop: bool = False, bf16_propagation: bool = False) -> abg_params:
+           early_stop: bool = False, bf16_propagation: bool = False,
+           bf16_contract: bool = False) -> abg_params:
     p = abg_params()
     lib().abg_params_default(C.byref(p))
     p.k, p.alpha, p.gamma, p.d, p.t_f, p.t_g = k, alpha, gamma, d, t_f, t_g
     p.oversample, p.power_iters, p.seed = oversample, power_iters, seed
     p.nci_flags = (ABG_NCI_PROCRUSTES if procrustes else 0) | (ABG_NCI_EARLY_STOP if early_stop else 0)
-    p.precision = ABG_BF16_PROPAGATION if bf16_propagation else ABG_PRECISION_FP32
+    p.precision = ((ABG_BF16_PROPAGATION if bf16_propagation else 0) |
+                   (ABG_BF16_CONTRACT if bf16_contract else 0))
     return p
 
 
@@ -347,15 +350,18 @@ def abg_random_features(zhat, n: int, d: int, seed: int, r_out, stream=None) -> 
 
 
 def abg_seed_factors(r, n: int, m: int, k: int, phi_out, h_out, sigma_out=None, oversample=10,
-                     power_iters=4, seed=0, stream=None):
+                     power_iters=4, seed=0, stream=None, bf16_contract: bool = False):
     _check(lib().abg_seed_factors(_ptr(r), n, m, _ld(r), k, oversample, power_iters, seed,
                                   _ptr(phi_out), _ld(phi_out), _ptr(h_out), _ld(h_out),
-                                  _ptr(sigma_out), _stream(stream)), "abg_seed_factors")
+                                  _ptr(sigma_out), ABG_BF16_CONTRACT if bf16_contract else 0,
+                                  _stream(stream)), "abg_seed_factors")
 
 
-def abg_onmf(r, n: int, m: int, k: int, t_f: int, phi, h, stream=None):
+def abg_onmf(r, n: int, m: int, k: int, t_f: int, phi, h, stream=None,
+             bf16_contract: bool = False):
     _check(lib().abg_onmf(_ptr(r), n, m, _ld(r), k, t_f, _ptr(phi), _ld(phi), _ptr(h), _ld(h),
-                          _stream(stream)), "abg_onmf")
+                          ABG_BF16_CONTRACT if bf16_contract else 0, _stream(stream)),
+           "abg_onmf")
 
 
 def abg_nci(phi, n: int, k: int, t_g: int, labels_out, margin_out=None, t_out=None, stream=None,

@@ -265,7 +265,8 @@ int gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s) {
             "gemm_nn: leading dimensions must be multiples of 4 and cover the width");
   if (rs.n_tiles == 0) return ABG_OK;
   bool tc = false;
-  ABG_TRY(tc_gemm_nn(rs, a, s, &tc));
+  if (a.A16) ABG_TRY(tc_gemm_nn16(rs, a, s, &tc));
+  if (!tc) ABG_TRY(tc_gemm_nn(rs, a, s, &tc));
   if (tc) return ABG_OK;
   NNK p{a.A, a.lda, a.B, a.ldb, a.b_seg, a.C, a.ldc, a.N, a.K, a.segN, a.segK,
         rs.tile_seg, rs.tile_row0, rs.tile_rows, (int)a.epi, a.aux, a.ldaux, a.aux2, a.ldaux2,
@@ -451,7 +452,8 @@ int gemm_tn(const RowSpace& rs, const TN& a, cudaStream_t s) {
   float* part;
   ABG_TRY(scr.get(&part, (size_t)rs.n_chunks * a.K * a.N));
   bool tc = false;
-  ABG_TRY(tc_gemm_tn(rs, a, part, s, &tc));
+  if (a.A16) ABG_TRY(tc_gemm_tn16(rs, a, part, s, &tc));
+  if (!tc) ABG_TRY(tc_gemm_tn(rs, a, part, s, &tc));
   if (tc)
     return reduce_pieces<float>(rs, false, part, (int64_t)a.K * a.N, a.N, a.segK, a.K, a.segN,
                                 a.N, a.C, a.ldc, a.c_seg, s);
@@ -504,7 +506,8 @@ int column_sums(const RowSpace& rs, int N, const float* A, int64_t lda, double* 
 // R[i] <- R'[i] / sqrt(max(R'[i].r_s, 1e-300)) with s the row's segment; one warp per row.
 __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t ldr,
                                const double* __restrict__ r, const int* __restrict__ row_seg,
-                               int* __restrict__ clamped) {
+                               int* __restrict__ clamped, __nv_bfloat16* __restrict__ R16,
+                               int64_t ldr16) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -518,12 +521,17 @@ __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t
   const bool clamp = !(dot > 1e-300);
   if (clamp) dot = 1e-300;
   const float inv = (float)(1.0 / sqrt(dot));
-  for (int c = lane; c < w2; c += 32) rp[c] *= inv;
+  for (int c = lane; c < w2; c += 32) {
+    const float v = rp[c] * inv;
+    rp[c] = v;
+    if (R16) R16[row * ldr16 + c] = __float2bfloat16_rn(v);
+  }
   if (clamp && lane == 0) atomicAdd(clamped + row_seg[row], 1);
 }
 
 int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, const float* qt,
-                    int64_t ldq, float* R, int64_t ldr, int* clamped_dev, cudaStream_t s) {
+                    int64_t ldq, float* R, int64_t ldr, int* clamped_dev, cudaStream_t s,
+                    __nv_bfloat16* R16, int64_t ldr16) {
   ABG_CHECK(ldr >= 2 * d && ldr % 4 == 0, "random_features: ldr must be >= 2d, multiple of 4");
   Scratch scr(s);
   double* cpart;
@@ -547,7 +555,8 @@ int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, c
   ABG_TRY(reduce_pieces<double>(rs, true, cpart, 2 * d, 2 * d, nullptr, 1, nullptr, 2 * d, r,
                                 2 * d, 2 * d, s));
   k_rf_normalise<<<(unsigned)ceil_div(rs.rows, 8), 256, 0, s>>>(rs.rows, 2 * d, R, ldr, r,
-                                                                 rs.row_seg, clamped_dev);
+                                                                 rs.row_seg, clamped_dev, R16,
+                                                                 ldr16);
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;

@@ -110,6 +110,9 @@ int csr_to_dense(const int64_t* ptr, const int32_t* col, const float* val, int64
                  float* dense, int64_t ld, cudaStream_t s);
 int bf16_to_f32(const __nv_bfloat16* x, int64_t ldx, int64_t rows, int cols, float* out,
                 int64_t ldo, cudaStream_t s);
+// out = x rounded to BF16 (nearest even)
+int f32_to_bf16(const float* x, int64_t ldx, int64_t rows, int cols, __nv_bfloat16* out,
+                int64_t ldo, cudaStream_t s);
 
 // ---- dense.cu (row spaces of batch.cuh; a plain solve is one segment) -------
 enum class Epi : int {
@@ -124,6 +127,10 @@ enum class Epi : int {
 struct NN {
   const float* A = nullptr;
   int64_t lda = 0;
+  // the same A stored in BF16 (row stride lda16): the product may then run on the BF16
+  // tensor-core kernel (B rounded to BF16, FP32 accumulation); A is the fallback
+  const __nv_bfloat16* A16 = nullptr;
+  int64_t lda16 = 0;
   const float* B = nullptr;
   int64_t ldb = 0, b_seg = 0;
   float* C = nullptr;
@@ -159,12 +166,18 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used);
 // when outside its limits (K, N <= 256, 16-byte rows) or ABG_TENSOR_CORES=0.
 struct TN;
 int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used);
+// BF16 forms of the two (kind::f16, FP32 accumulation) for a.A16 != null, no segK, and in
+// the TN case K, N <= 256.
+int tc_gemm_nn16(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used);
+int tc_gemm_tn16(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used);
 // Reads and clears the tensor-core kernels' wait flag (synchronises s).
 int tc_wait_flag(cudaStream_t s, int* flag);
 // C_s (K_s x N_s, FP64, at C + s*c_seg, row stride ldc) = A^T B over the rows of segment s.
 struct TN {
   const float* A = nullptr;
   int64_t lda = 0;
+  const __nv_bfloat16* A16 = nullptr;  // as NN::A16
+  int64_t lda16 = 0;
   const float* B = nullptr;
   int64_t ldb = 0;
   int K = 0, N = 0;
@@ -179,8 +192,10 @@ int column_sums(const RowSpace& rs, int N, const float* A, int64_t lda, double* 
                 cudaStream_t s);
 // Eqs. 13-14: R (2d wide) from zhat (d wide) with Qt_s = Q_s^T at qt + s*d*ldq; per-segment r;
 // clamped_dev[s] counts clamped rows.
+// R16 (may be null): a BF16 copy of R (row stride ldr16) written by the same pass.
 int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, const float* qt,
-                    int64_t ldq, float* R, int64_t ldr, int* clamped_dev, cudaStream_t s);
+                    int64_t ldq, float* R, int64_t ldr, int* clamped_dev, cudaStream_t s,
+                    __nv_bfloat16* R16 = nullptr, int64_t ldr16 = 0);
 // Eq. 16 per segment (H_s at H + s*hseg, m x k_s; A_s, G_s FP64 slabs).
 int nmf_update_h(int nseg, int m, const int* segk, int kmax, float* H, int64_t ldh, int64_t hseg,
                  const double* A, int64_t lda, int64_t aseg, const double* G, int64_t ldg,
@@ -224,6 +239,8 @@ struct RsvdIn {
   int m = 0;                       // columns of A (same for every segment)
   const float* A = nullptr;        // dense rows x m
   int64_t lda = 0;
+  const __nv_bfloat16* A16 = nullptr;  // optional BF16 copy of A for the BF16 products
+  int64_t lda16 = 0;
   // or a CSR whose column j of segment s is stored as s*m + j, and the CSR of the
   // transposes with row s*m + j listing segment s's rows (global row ids)
   const int64_t* ptr = nullptr;

@@ -618,6 +618,8 @@ static int apply_a(const RsvdIn& in, const int* segl, int lmax, const float* Om,
     NN a;
     a.A = in.A;
     a.lda = in.lda;
+    a.A16 = in.A16;
+    a.lda16 = in.lda16;
     a.B = Om;
     a.ldb = ldo;
     a.b_seg = (int64_t)in.m * ldo;
@@ -640,6 +642,8 @@ static int apply_at(const RsvdIn& in, const int* segl, int lmax, const float* Q,
     TN t;
     t.A = in.A;
     t.lda = in.lda;
+    t.A16 = in.A16;
+    t.lda16 = in.lda16;
     t.B = Q;
     t.ldb = ldq;
     t.K = in.m;

@@ -35,7 +35,8 @@ int abg::check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, i
             "attribute reduction needs d + oversample <= 1024");
   ABG_CHECK((p->nci_flags & ~(ABG_NCI_PROCRUSTES | ABG_NCI_EARLY_STOP)) == 0,
             "unknown nci_flags %d", p->nci_flags);
-  ABG_CHECK((p->precision & ~ABG_BF16_PROPAGATION) == 0, "unknown precision %d", p->precision);
+  ABG_CHECK((p->precision & ~(ABG_BF16_CONTRACT | ABG_BF16_PROPAGATION)) == 0,
+            "unknown precision %d", p->precision);
   ABG_CHECK(p->reserved == 0, "abg_params.reserved must be 0");
   *d_eff = d;
   return ABG_OK;
@@ -54,11 +55,12 @@ struct SolveOut {
 };
 
 // Attributes the propagation reads: the graph's own (dense), a densified CSR, or the
-// per-segment SVD-reduced X' of Eq. 15.
+// per-segment SVD-reduced X' of Eq. 15. bf16_contract: the products of that SVD read BF16
+// attributes directly (BF16 tensor-core kernels, FP32 accumulation).
 int prepare_attributes(const abg_graph* g, const RowSpace& rs, int d, int oversample,
                        int power_iters, const std::vector<uint64_t>& seeds, Scratch& scr,
                        cudaStream_t s, const float** xf, const __nv_bfloat16** xb, int64_t* ldx,
-                       int* breakdowns) {
+                       int* breakdowns, bool bf16_contract = false) {
   *xf = nullptr;
   *xb = nullptr;
   if (d == g->d_u) {
@@ -107,6 +109,10 @@ int prepare_attributes(const abg_graph* g, const RowSpace& rs, int d, int oversa
     ABG_TRY(bf16_to_f32((const __nv_bfloat16*)g->x, g->ldx, g->n_u, (int)g->ldx, xf32, g->ldx, s));
     in.A = xf32;
     in.lda = g->ldx;
+    if (bf16_contract) {
+      in.A16 = (const __nv_bfloat16*)g->x;
+      in.lda16 = g->ldx;
+    }
   }
   RsvdOut out;
   out.left = xr;
@@ -118,9 +124,10 @@ int prepare_attributes(const abg_graph* g, const RowSpace& rs, int d, int oversa
   return ABG_OK;
 }
 
+// R16 (may be null): BF16 copy of R for the two products with R (R^T Phi and R H).
 int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int64_t ldr,
                     int t_f, float* phi, int64_t ldphi, float* H, int64_t ldh, int64_t hseg,
-                    cudaStream_t s) {
+                    cudaStream_t s, const __nv_bfloat16* R16 = nullptr, int64_t ldr16 = 0) {
   if (t_f == 0) return ABG_OK;
   const int nseg = rs.nseg, kmax = ss.k_max;
   const int64_t kk = round_up(kmax, 4);
@@ -140,6 +147,8 @@ int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int 
     TN ta;
     ta.A = R;
     ta.lda = ldr;
+    ta.A16 = R16;
+    ta.lda16 = ldr16;
     ta.B = cur;
     ta.ldb = ldphi;
     ta.K = m;
@@ -164,6 +173,8 @@ int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int 
     NN pr;
     pr.A = R;
     pr.lda = ldr;
+    pr.A16 = R16;
+    pr.lda16 = ldr16;
     pr.B = H;
     pr.ldb = ldh;
     pr.b_seg = hseg;
@@ -222,7 +233,7 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   const __nv_bfloat16* xb;
   int64_t ldx;
   ABG_TRY(prepare_attributes(g, rs, d, p.oversample, p.power_iters, seeds, scr, s, &xf, &xb, &ldx,
-                             o.breakdowns));
+                             o.breakdowns, (p.precision & ABG_BF16_CONTRACT) != 0));
   const int64_t ldz = round_up(d, 4);
   float* zhat;
   ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
@@ -239,7 +250,10 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   const int64_t ldr = round_up(m, 4);
   float* R;
   ABG_TRY(scr.get(&R, (size_t)n * ldr));
-  ABG_TRY(random_features(rs, zhat, d, ldz, qt, ldz, R, ldr, o.clamped, s));
+  __nv_bfloat16* R16 = nullptr;  // BF16 copy of R for the products with R
+  const int64_t ldr16 = round_up(m, 8);
+  if (p.precision & ABG_BF16_CONTRACT) ABG_TRY(scr.get(&R16, (size_t)n * ldr16));
+  ABG_TRY(random_features(rs, zhat, d, ldz, qt, ldz, R, ldr, o.clamped, s, R16, ldr16));
   if (ev) ABG_CUDA(cudaEventRecord(ev[3], s));
   // ---- Algorithm 2 ----
   const int kmax = ss.k_max;
@@ -253,6 +267,8 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   in.m = m;
   in.A = R;
   in.lda = ldr;
+  in.A16 = R16;
+  in.lda16 = ldr16;
   RsvdOut out;
   out.left = phi;
   out.ldl = kk;
@@ -261,7 +277,7 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   out.ldr = kk;
   out.rseg = hseg;
   ABG_TRY(rsvd(in, ss, 0, p.power_iters, ABG_STREAM_OMEGA_R, out, o.breakdowns, s));
-  ABG_TRY(onmf_iterations(rs, ss, R, m, ldr, p.t_f, phi, kk, H, kk, hseg, s));
+  ABG_TRY(onmf_iterations(rs, ss, R, m, ldr, p.t_f, phi, kk, H, kk, hseg, s, R16, ldr16));
   if (ev) ABG_CUDA(cudaEventRecord(ev[4], s));
   // ---- Algorithm 3 ----
   ABG_TRY(nci_run(rs, ss, phi, kk, p.t_g, p.nci_flags, o.labels, nullptr, nullptr, o.counters,
@@ -398,6 +414,7 @@ ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {
   else
     b += 4 * g->n_v * ld;                // W
   b += 4 * n * ldr;                      // R
+  if (p->precision & ABG_BF16_CONTRACT) b += 2 * n * round_up(2 * d, 8);  // BF16 copy of R
   b += 4 * n * ll * 2;                   // randomized SVD blocks
   b += 4 * n * kk * 4;                   // Phi (x2), P, spare
   b += 8 * n;                            // labels, row segments
@@ -514,7 +531,7 @@ ABG_API int abg_random_features(const float* zhat, int64_t n, int32_t d, int64_t
 ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k,
                              int32_t oversample, int32_t power_iters, uint64_t seed,
                              float* phi_out, int64_t ldphi, float* h_out, int64_t ldh,
-                             double* sigma_out, void* stream) {
+                             double* sigma_out, int32_t precision, void* stream) {
   ABG_CHECK(r && phi_out && h_out && n >= 1 && m >= 1, "bad arguments");
   ABG_CHECK(k >= 1 && k <= m && k <= n && k <= kMaxK, "need 1 <= k <= min(n, m, %d)", kMaxK);
   ABG_CHECK(ldr >= m && ldr % 4 == 0 && ldphi >= k && ldphi % 4 == 0 && ldh >= k && ldh % 4 == 0,
@@ -530,11 +547,20 @@ ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, 
   int* bd;
   ABG_TRY(scr.get(&bd, 1));
   ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
+  ABG_CHECK(precision == ABG_PRECISION_FP32 || precision == ABG_BF16_CONTRACT,
+            "unknown precision %d", precision);
   RsvdIn in;
   in.rows = &rs;
   in.m = m;
   in.A = r;
   in.lda = ldr;
+  if (precision == ABG_BF16_CONTRACT) {
+    __nv_bfloat16* r16;
+    in.lda16 = round_up(m, 8);
+    ABG_TRY(scr.get(&r16, (size_t)n * in.lda16));
+    ABG_TRY(f32_to_bf16(r, ldr, n, m, r16, in.lda16, s));
+    in.A16 = r16;
+  }
   RsvdOut out;
   out.left = phi_out;
   out.ldl = ldphi;
@@ -546,7 +572,8 @@ ABG_API int abg_seed_factors(const float* r, int64_t n, int32_t m, int64_t ldr, 
 }
 
 ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t k, int32_t t_f,
-                     float* phi, int64_t ldphi, float* h, int64_t ldh, void* stream) {
+                     float* phi, int64_t ldphi, float* h, int64_t ldh, int32_t precision,
+                     void* stream) {
   ABG_CHECK(r && phi && h && n >= 1 && m >= 1 && k >= 1 && k <= kMaxK && t_f >= 0, "bad arguments");
   ABG_CHECK(ldr >= m && ldr % 4 == 0 && ldphi >= k && ldphi % 4 == 0 && ldh >= k && ldh % 4 == 0,
             "leading dimensions must cover the width and be multiples of 4");
@@ -556,7 +583,16 @@ ABG_API int abg_onmf(const float* r, int64_t n, int32_t m, int64_t ldr, int32_t 
   ABG_TRY(single_rows(n, &rs, scr, s));
   SegSizes ss;
   ABG_TRY(segsizes_build(&ss, {k}, {k}, {0}, scr, s));
-  return onmf_iterations(rs, ss, r, m, ldr, t_f, phi, ldphi, h, ldh, (int64_t)m * ldh, s);
+  ABG_CHECK(precision == ABG_PRECISION_FP32 || precision == ABG_BF16_CONTRACT,
+            "unknown precision %d", precision);
+  __nv_bfloat16* r16 = nullptr;
+  const int64_t ld16 = round_up(m, 8);
+  if (precision == ABG_BF16_CONTRACT) {
+    ABG_TRY(scr.get(&r16, (size_t)n * ld16));
+    ABG_TRY(f32_to_bf16(r, ldr, n, m, r16, ld16, s));
+  }
+  return onmf_iterations(rs, ss, r, m, ldr, t_f, phi, ldphi, h, ldh, (int64_t)m * ldh, s, r16,
+                         ld16);
 }
 
 ABG_API int abg_nci(const float* phi, int64_t n, int32_t k, int64_t ldphi, int32_t t_g,

@@ -1042,4 +1042,22 @@ int bf16_to_f32(const __nv_bfloat16* x, int64_t ldx, int64_t rows, int cols, flo
   return ABG_OK;
 }
 
+__global__ void k_f32_to_bf16(const float* __restrict__ x, int64_t ldx, int64_t rows, int cols,
+                              __nv_bfloat16* __restrict__ out, int64_t ldo) {
+  int64_t total = rows * (int64_t)cols;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = t / cols;
+    int c = (int)(t - r * cols);
+    out[r * ldo + c] = __float2bfloat16_rn(x[r * ldx + c]);
+  }
+}
+
+int f32_to_bf16(const float* x, int64_t ldx, int64_t rows, int cols, __nv_bfloat16* out,
+                int64_t ldo, cudaStream_t s) {
+  k_f32_to_bf16<<<num_sms() * 8, 256, 0, s>>>(x, ldx, rows, cols, out, ldo); ::abg::note_launch();
+  ABG_LAUNCH_CHECK();
+  return ABG_OK;
+}
+
 }  // namespace abg

@@ -18,6 +18,13 @@
 // per call by a small kernel (transposed to K-major, zero outside K_s x N_s).
 // Every mbarrier wait is bounded; a wait that runs out sets a device flag
 // (read by tc_wait_flag) and the CTA still frees its tensor memory.
+//
+// BF16 variants (tcgen05.mma kind::f16, fp32 accumulation) serve products whose
+// tall operand is stored in BF16 (the random-feature matrix R when BF16
+// contractions are selected): k_tc_nn16 takes the A tile from TMA as is (no
+// split warps) with B rounded to BF16 once and kept in shared memory;
+// k_tc_tn16 reads the A rows as MN-major operand tiles straight from TMA and
+// only rounds the fp32 B rows to BF16 (no transpose).
 #include <cstdlib>
 #include <cstring>
 
@@ -63,6 +70,7 @@ struct TcArgs {
   uint32_t stage_bytes;
   uint32_t b_bytes;
   uint32_t tmem_cols;
+  int b_resident;  // BF16 kernel: all K blocks of B stay in shared memory (one segment)
 };
 
 __device__ __forceinline__ float rna_tf32(float x) {
@@ -95,6 +103,34 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// instruction descriptor: D f32, A/B bf16, M = 128, N = n; a_mn / b_mn: operand is MN-major
+__host__ __device__ constexpr uint32_t bf16_idesc(int n, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// shared-memory matrix descriptor, MN-major with 128-byte swizzle: each K row holds 64 bf16
+// of the MN dimension in 128 bytes, 8 K rows form a 1024-byte atom (the next 8 K rows 1024
+// bytes on), and the next 64 MN elements start lbo bytes on
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t addr, uint32_t lbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;     // leading byte offset: next 64 MN elements
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8 K rows
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+  return d;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -670,6 +706,407 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 NN: C = A16 B_s with A16 (rows x K, bf16, row-major) and B_s rounded to bf16 once.
+// K moves in 64-column blocks (one 128-byte swizzle row of bf16), four UMMA K = 16 steps
+// each. With one segment all of B stays in shared memory; otherwise each stage carries its
+// B block. No split warps: the A tile goes from TMA to the MMAs untouched.
+//   warp 0: TMA producer   warp 1: TMEM owner + MMA issuer   warps 2-5: epilogue
+// ---------------------------------------------------------------------------
+constexpr int kBK16 = 64;                              // bf16 K per stage
+constexpr uint32_t kA16Bytes = kTcM * kBK16 * 2;       // 16 KiB
+constexpr int kNn16Threads = 192;
+
+// B16 (segment s rows s*Np .. s*Np + Np, K-major bf16, Kp columns) from B_s (K x N fp32)
+__global__ void k_tc_prep_b16(const float* __restrict__ B, int64_t ldb, int64_t b_seg,
+                              const int* __restrict__ segK, int K, const int* __restrict__ segN,
+                              int N, int Np, int Kp, __nv_bfloat16* __restrict__ out) {
+  const int sg = blockIdx.y;
+  const int Ks = segK ? segK[sg] : K;
+  const int Ns = segN ? segN[sg] : N;
+  const float* Bs = B + sg * b_seg;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Np * Kp;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / Kp), k = (int)(e % Kp);
+    const float x = (n < Ns && k < Ks) ? Bs[(int64_t)k * ldb + n] : 0.f;
+    out[((int64_t)sg * Np + n) * Kp + k] = __float2bfloat16_rn(x);
+  }
+}
+
+__global__ void __launch_bounds__(kNn16Threads, 1)
+    k_tc_nn16(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+              const TcArgs p, int64_t n_tiles) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = p.stages;
+  const uint32_t bres_bytes = p.b_resident ? (uint32_t)p.nkb * p.b_bytes : 0u;
+  unsigned char* bres = smem;
+  unsigned char* stg = smem + bres_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + (size_t)S * p.stage_bytes);
+  const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * S, bfull = full0 + 16 * S,
+                 tfull0 = bfull + 8, tempty0 = tfull0 + 16;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    mbar_init(bfull, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t acc_cols = p.tmem_cols / 2;
+  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+
+  if (warp == 0) {
+    if (lane == 0 && !bad) {  // producer
+      if (p.b_resident) {     // every K block of B, once
+        mbar_expect_tx(bfull, bres_bytes);
+        for (int kb = 0; kb < p.nkb; ++kb)
+          tma_load_2d(smem_addr(bres + (size_t)kb * p.b_bytes), &bmap, kb * kBK16, 0, bfull);
+      }
+      const uint32_t tx = kA16Bytes + (p.b_resident ? 0u : p.b_bytes);
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t n = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x) {
+        const int sg = p.tile_seg[tile];
+        const int row0 = (int)p.tile_row0[tile];
+        for (int kb = 0; kb < p.nkb; ++kb, ++n) {
+          if (n >= S && !mbar_wait_bounded(empty0 + 8 * s, ph ^ 1u)) {
+            bad = true;
+            break;
+          }
+          const uint32_t st = smem_addr(stg + (size_t)s * p.stage_bytes);
+          mbar_expect_tx(full0 + 8 * s, tx);
+          tma_load_2d(st, &amap, kb * kBK16, row0, full0 + 8 * s);
+          if (!p.b_resident)
+            tma_load_2d(st + kA16Bytes, &bmap, kb * kBK16, sg * p.Np, full0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && !bad) {  // MMA issuer
+      const uint32_t idesc = bf16_idesc(p.Np, false, false);
+      if (p.b_resident && !mbar_wait_bounded(bfull, 0)) bad = true;
+      tc_fence_after();
+      int s = 0;
+      uint32_t ph = 0;
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles && !bad; tile += gridDim.x, ++it) {
+        const int bsel = it & 1;
+        if (it >= 2 && !mbar_wait_bounded(tempty0 + 8 * bsel, ((it >> 1) - 1) & 1)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tacc = tmem + (uint32_t)bsel * acc_cols;
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          if (!mbar_wait_bounded(full0 + 8 * s, ph)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_addr(stg + (size_t)s * p.stage_bytes);
+          const uint32_t b = p.b_resident ? smem_addr(bres + (size_t)kb * p.b_bytes)
+                                          : a + kA16Bytes;
+#pragma unroll
+          for (int j = 0; j < kBK16 / 16; ++j) {  // UMMA K = 16 bf16 = 32 bytes
+            const uint32_t off = 32u * j;
+            mma_bf16(tacc, sw128_desc(a + off), sw128_desc(b + off), idesc, (kb | j) != 0);
+          }
+          mma_commit(empty0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (bad) break;
+        mma_commit(tfull0 + 8 * bsel);
+      }
+    }
+  } else {
+    // epilogue: warps 2-5 own TMEM lane quarters 2, 3, 0, 1
+    const int quad = warp & 3;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+      const int bsel = it & 1;
+      bad = bad || !mbar_wait_bounded(tfull0 + 8 * bsel, (it >> 1) & 1);
+      bad = __any_sync(0xffffffffu, bad);
+      if (bad) break;
+      tc_fence_after();
+      const int sg = p.tile_seg[tile];
+      const int Ns = p.segN ? p.segN[sg] : p.N;
+      tc_epilogue_row<false>(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, sg,
+                             p.tile_row0[tile], p.tile_rows[tile], Ns);
+      tc_fence_before();
+      mbar_arrive(tempty0 + 8 * bsel);
+    }
+  }
+  if (bad) atomicExch(&g_tc_wait_err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BF16 TN: partial[c] (K x N) = A16[rows of chunk c]^T B[rows of chunk c]. The reduction
+// index (rows) is UMMA K for both operands, and both are stored with their M / N index
+// contiguous, so both go to the MMAs as MN-major tiles: A16 arrives from TMA in 64-row x
+// 64-column boxes (128-byte swizzle) and is used in place; the converter warps round each
+// 64-row block of the fp32 B rows to bf16 into the same MN-major layout (zeros for rows
+// past the chunk and columns past N_s). A raw stage is free once the MMAs have read its A
+// boxes (commit) and the converters its B rows (128 arrivals).
+//   warp 0: TMA producer   warp 1: TMEM owner + MMA issuer
+//   warps 2-5: B converters   warps 6-9: epilogue (partials to global)
+// ---------------------------------------------------------------------------
+constexpr int kTn16Rows = 64;                          // rows per block (4 UMMA K steps)
+constexpr uint32_t kMnBox = kTn16Rows * 128;           // one 64 x 64 bf16 box: 8 KiB
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_tn16(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+              const TnArgs p, int64_t n_chunks) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_slot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = p.stages;
+  const int NO = p.nops;
+  unsigned char* ops = smem;                                   // converted B sets
+  unsigned char* raw = smem + (size_t)NO * p.op_bytes;         // A boxes + raw B rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(raw + (size_t)S * p.raw_bytes);
+  const uint32_t rfull0 = smem_addr(bars), rempty0 = rfull0 + 8 * S, opfull0 = rfull0 + 16 * S,
+                 opempty0 = opfull0 + 8 * NO, tfull = opempty0 + 8 * NO, tempty = tfull + 8;
+  // 64-column boxes of A that hold columns < K (the rest of the 128 * mblk operand rows only
+  // feed accumulator rows >= K, which the epilogue drops)
+  const int nbox_a = (p.K + 63) / 64;
+  const int nch_b = (p.Np + 63) / 64;             // 64-column chunks of the B operand
+  const uint32_t tx = (uint32_t)nbox_a * kMnBox + (uint32_t)kTn16Rows * p.nb_box * 4;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(rfull0 + 8 * i, 1);
+      mbar_init(rempty0 + 8 * i, 129);  // MMA commit + 128 converter threads
+    }
+    for (int i = 0; i < NO; ++i) {
+      mbar_init(opfull0 + 8 * i, 128);
+      mbar_init(opempty0 + 8 * i, 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t n = 0;
+      for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+        const int64_t r0 = p.chunk_row0[c];
+        const int nb = (p.chunk_rows[c] + kTn16Rows - 1) / kTn16Rows;
+        for (int b = 0; b < nb; ++b, ++n) {
+          if (n >= S && !mbar_wait_bounded(rempty0 + 8 * s, ph ^ 1u)) {
+            bad = true;
+            break;
+          }
+          const uint32_t st = smem_addr(raw + (size_t)s * p.raw_bytes);
+          const int y = (int)(r0 + b * kTn16Rows);
+          mbar_expect_tx(rfull0 + 8 * s, tx);
+          for (int q = 0; q < nbox_a; ++q)
+            tma_load_2d(st + (uint32_t)q * kMnBox, &amap, q * 64, y, rfull0 + 8 * s);
+          tma_load_2d(st + p.raw_a_bytes, &bmap, 0, y, rfull0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = bf16_idesc(p.Np, true, true);
+      int s = 0, os = 0;
+      uint32_t ph = 0, op_ph = 0;
+      int it = 0;
+      for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x, ++it) {
+        if (it >= 1 && !mbar_wait_bounded(tempty, (it - 1) & 1)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const int nb = (p.chunk_rows[c] + kTn16Rows - 1) / kTn16Rows;
+        for (int b = 0; b < nb; ++b) {
+          if (!mbar_wait_bounded(rfull0 + 8 * s, ph) ||
+              !mbar_wait_bounded(opfull0 + 8 * os, op_ph)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_addr(raw + (size_t)s * p.raw_bytes);
+          const uint32_t b0 = smem_addr(ops + (size_t)os * p.op_bytes);
+          for (int mb = 0; mb < p.mblk; ++mb) {
+            const uint32_t dcol = tmem + (uint32_t)(mb * p.Np);
+            const uint32_t am = a0 + (uint32_t)mb * 2 * kMnBox;
+#pragma unroll
+            for (int j = 0; j < kTn16Rows / 16; ++j) {  // 16 rows = two 8-row groups
+              const uint32_t off = 2048u * j;
+              mma_bf16(dcol, sw128_mn_desc(am + off, kMnBox), sw128_mn_desc(b0 + off, kMnBox),
+                       idesc, (b | j) != 0);
+            }
+          }
+          mma_commit(rempty0 + 8 * s);   // A boxes read
+          mma_commit(opempty0 + 8 * os);  // B set read
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+          if (++os == NO) {
+            os = 0;
+            op_ph ^= 1u;
+          }
+        }
+        if (bad) break;
+        mma_commit(tfull);
+      }
+    }
+  } else if (warp < 6) {
+    // B rows (fp32, nb_box wide) -> bf16 MN-major 128-byte swizzled chunks of 64 columns
+    const int t = threadIdx.x - 64;
+    int s = 0, os = 0;
+    uint32_t ph = 0, op_ph = 0;
+    int64_t n = 0;
+    for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+      const int sg = p.chunk_seg[c];
+      const int Ns = p.segN ? p.segN[sg] : p.N;
+      const int rows = p.chunk_rows[c];
+      const int nb = (rows + kTn16Rows - 1) / kTn16Rows;
+      for (int b = 0; b < nb; ++b, ++n) {
+        if (!mbar_wait_bounded(rfull0 + 8 * s, ph) ||
+            (n >= NO && !mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u))) {
+          bad = true;
+          break;
+        }
+        const float* rb = reinterpret_cast<const float*>(raw + (size_t)s * p.raw_bytes +
+                                                         p.raw_a_bytes);
+        const int mvalid = rows - b * kTn16Rows;
+        unsigned char* o = ops + (size_t)os * p.op_bytes;
+        const int units = kTn16Rows * nch_b * 8;  // 16-byte units of the operand
+        for (int q = t; q < units; q += 128) {
+          const int row = q / (nch_b * 8), cu = q % (nch_b * 8);
+          const int ch = cu >> 3, u = cu & 7;
+          const int n0 = ch * 64 + u * 8;
+          float v[8];
+          if (row < mvalid && n0 + 7 < Ns) {
+            const float4 x0 = *reinterpret_cast<const float4*>(rb + row * p.nb_box + n0);
+            const float4 x1 = *reinterpret_cast<const float4*>(rb + row * p.nb_box + n0 + 4);
+            v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+            v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              v[e] = (row < mvalid && n0 + e < Ns) ? rb[row * p.nb_box + n0 + e] : 0.f;
+          }
+          uint4 w;
+          __nv_bfloat162 h;
+          h = __floats2bfloat162_rn(v[0], v[1]);
+          w.x = *reinterpret_cast<const uint32_t*>(&h);
+          h = __floats2bfloat162_rn(v[2], v[3]);
+          w.y = *reinterpret_cast<const uint32_t*>(&h);
+          h = __floats2bfloat162_rn(v[4], v[5]);
+          w.z = *reinterpret_cast<const uint32_t*>(&h);
+          h = __floats2bfloat162_rn(v[6], v[7]);
+          w.w = *reinterpret_cast<const uint32_t*>(&h);
+          *reinterpret_cast<uint4*>(o + (uint32_t)ch * kMnBox + (uint32_t)row * 128 +
+                                    (uint32_t)((u ^ (row & 7)) * 16)) = w;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+        mbar_arrive(rempty0 + 8 * s);
+        mbar_arrive(opfull0 + 8 * os);
+        if (++os == NO) {
+          os = 0;
+          op_ph ^= 1u;
+        }
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  } else {
+    // epilogue: M block rows -> partial rows (K index), N columns
+    const int quad = warp & 3;
+    int it = 0;
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
+      bad = bad || !mbar_wait_bounded(tfull, it & 1);
+      bad = __any_sync(0xffffffffu, bad);
+      if (bad) break;
+      tc_fence_after();
+      float* pc = p.part + c * (int64_t)p.K * p.N;
+      for (int mb = 0; mb < p.mblk; ++mb) {
+        const int ka = mb * kTcM + quad * 32 + lane;
+        for (int c0 = 0; c0 < p.Np; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mb * p.Np + c0), v);
+          if (ka >= p.K) continue;
+          float* prow = pc + (int64_t)ka * p.N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < p.N) prow[c0 + j] = v[j];
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty);
+    }
+  }
+  if (bad) atomicExch(&g_tc_wait_err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
 bool tc_disabled() {
   const char* e = std::getenv("ABG_TENSOR_CORES");
   return e && e[0] == '0';
@@ -850,6 +1287,157 @@ int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, boo
   ABG_TRY(raise_smem_limit((const void*)k_tc_tn, smem));
   const unsigned grid = (unsigned)std::min<int64_t>(rs.n_chunks, num_sms());
   k_tc_tn<<<grid, kTcThreads, smem, s>>>(amap, bmap, p, rs.n_chunks);
+  note_launch();
+  note_tc_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
+int tc_gemm_nn16(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
+  *used = false;
+  if (!a.A16 || a.segK || a.argmax || a.sincos || tc_disabled()) return ABG_OK;
+  if (a.ldc % 4 != 0 || reinterpret_cast<uintptr_t>(a.C) % 16 != 0) return ABG_OK;
+  if (a.N > 256 || rs.n_tiles == 0 || rs.rows > INT32_MAX) return ABG_OK;
+  if (a.lda16 % 8 != 0 || reinterpret_cast<uintptr_t>(a.A16) % 16 != 0) return ABG_OK;
+  const auto enc = tensor_map_encoder();
+  if (!enc) return ABG_OK;
+  const int nseg = rs.nseg;
+  const int Np = (int)round_up(a.N, 16);
+  const int nkb = (int)ceil_div(a.K, kBK16);
+  const int Kp = nkb * kBK16;
+  if ((int64_t)nseg * Np > INT32_MAX) return ABG_OK;
+  Scratch scr(s);
+  __nv_bfloat16* b16;
+  ABG_TRY(scr.get(&b16, (size_t)nseg * Np * Kp));
+  {
+    const int64_t work = (int64_t)Np * Kp;
+    dim3 g((unsigned)std::min<int64_t>(ceil_div(work, 256), 256), (unsigned)nseg);
+    k_tc_prep_b16<<<g, 256, 0, s>>>(a.B, a.ldb, a.b_seg, nullptr, a.K, a.segN, a.N, Np, Kp, b16);
+    note_launch();
+    ABG_LAUNCH_CHECK();
+  }
+  CUtensorMap amap, bmap;
+  const cuuint32_t es[2] = {1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.lda16 * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK16, (cuuint32_t)kTcM};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.A16), dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)nseg * Np};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK16, (cuuint32_t)Np};
+    if (enc(&bmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, b16, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  TcArgs p{};
+  p.nkb = nkb;
+  p.Np = Np;
+  p.N = a.N;
+  p.K = a.K;
+  p.segN = a.segN;
+  p.tile_seg = rs.tile_seg;
+  p.tile_row0 = rs.tile_row0;
+  p.tile_rows = rs.tile_rows;
+  p.C = a.C;
+  p.ldc = a.ldc;
+  p.epi = (int)a.epi;
+  p.aux = a.aux;
+  p.ldaux = a.ldaux;
+  p.aux2 = a.aux2;
+  p.ldaux2 = a.ldaux2;
+  p.sign = a.sign;
+  p.sign_seg = a.sign_seg;
+  p.b_bytes = (uint32_t)Np * 128;  // one 64-wide K block of B
+  const size_t cap = 220 * 1024 - 1024 - 8 * (2 * 8 + 5);
+  p.b_resident = nseg == 1 && (size_t)nkb * p.b_bytes + 2 * kA16Bytes <= cap;
+  p.stage_bytes = kA16Bytes + (p.b_resident ? 0u : p.b_bytes);
+  const size_t bres = p.b_resident ? (size_t)nkb * p.b_bytes : 0;
+  p.stages = (int)std::min<size_t>(8, (cap - bres) / p.stage_bytes);
+  if (p.stages < 2) return ABG_OK;
+  p.tmem_cols = 64;
+  while ((int)p.tmem_cols < 2 * Np) p.tmem_cols *= 2;
+  const size_t smem = bres + (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 5);
+  ABG_TRY(raise_smem_limit((const void*)k_tc_nn16, smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(rs.n_tiles, num_sms());
+  k_tc_nn16<<<grid, kNn16Threads, smem, s>>>(amap, bmap, p, rs.n_tiles);
+  note_launch();
+  note_tc_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
+int tc_gemm_tn16(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used) {
+  *used = false;
+  if (!a.A16 || a.segK || tc_disabled() || a.K > 256 || a.N > 256 || rs.n_chunks == 0)
+    return ABG_OK;
+  if (a.lda16 % 8 != 0 || a.ldb % 4 != 0 || reinterpret_cast<uintptr_t>(a.A16) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(a.B) % 16 != 0 || rs.rows > INT32_MAX)
+    return ABG_OK;
+  const auto enc = tensor_map_encoder();
+  if (!enc) return ABG_OK;
+  TnArgs p{};
+  p.K = a.K;
+  p.N = a.N;
+  p.Np = (int)round_up(a.N, 16);
+  p.mblk = (int)ceil_div(a.K, kTcM);
+  p.nb_box = (int)round_up(a.N, 4);
+  p.segN = a.segN;
+  p.chunk_seg = rs.chunk_seg;
+  p.chunk_row0 = rs.chunk_row0;
+  p.chunk_rows = rs.chunk_rows;
+  p.part = part;
+  p.raw_a_bytes = 2u * p.mblk * kMnBox;
+  p.raw_bytes = (uint32_t)round_up((int64_t)p.raw_a_bytes + (int64_t)kTn16Rows * p.nb_box * 4, 1024);
+  p.op_bytes = (uint32_t)ceil_div(p.Np, 64) * kMnBox;
+  p.tmem_cols = 32;
+  while ((int)p.tmem_cols < p.mblk * p.Np) p.tmem_cols *= 2;
+  if (p.tmem_cols > 512) return ABG_OK;
+  size_t smem = 0;
+  bool fits = false;
+  for (p.nops = 2; p.nops >= 1 && !fits; --p.nops) {
+    for (p.stages = 4; p.stages >= 2; --p.stages) {
+      smem = 1024 + (size_t)p.nops * p.op_bytes + (size_t)p.stages * p.raw_bytes +
+             8 * (2 * p.stages + 2 * p.nops + 2);
+      if (smem <= 220 * 1024) {
+        fits = true;
+        break;
+      }
+    }
+    if (fits) break;
+  }
+  if (!fits) return ABG_OK;
+  CUtensorMap amap, bmap;
+  const cuuint32_t es[2] = {1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.K, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.lda16 * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kTn16Rows};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.A16), dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)a.N, (cuuint64_t)rs.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.ldb * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)p.nb_box, (cuuint32_t)kTn16Rows};
+    if (enc(&bmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.B), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ABG_OK;
+  }
+  ABG_TRY(raise_smem_limit((const void*)k_tc_tn16, smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(rs.n_chunks, num_sms());
+  k_tc_tn16<<<grid, kTcThreads, smem, s>>>(amap, bmap, p, rs.n_chunks);
   note_launch();
   note_tc_launch();
   ABG_LAUNCH_CHECK();
