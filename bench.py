@@ -275,7 +275,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     g = synth.make_config3(seed=rank, scale=args.scale)
     csc = csc_of(g)
     p = abg.params(**PARAMS, procrustes=args.nci == "procrustes",
-                   bf16_propagation=args.precision == "bf16")
+                   bf16_propagation=args.precision in ("bf16-propagation", "bf16"),
+                   bf16_contract=args.precision in ("bf16-contract", "bf16"))
     stream = torch.cuda.current_stream()
     graph = abg.abg_create(g, device=local_rank, stream=stream, csc=csc)
     labels = torch.empty(g.n_u, dtype=torch.int32).pin_memory().numpy()
@@ -334,13 +335,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
-    pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"], args.precision)
+    prop_prec = "bf16" if args.precision in ("bf16-propagation", "bf16") else "fp32"
+    pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"], prop_prec)
     achieved = pbytes / (prop_ms / 1e3) / 1e9
     value = world * args.steps / elapsed
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32+bf16",
         "data": "synthetic",
         "config": dict(workload_of(g, args.scale), nnz=int(g.nnz),
                        parallelism=f"{world} independent solves "
@@ -351,7 +354,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "spmm_hbm_gbs": achieved,
         "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
                               "objective"], phase_ms)),
-        "roofline": roofline_of(pbytes, prop_ms, peak, peak_kind, args.scale, args.precision),
+        "roofline": roofline_of(pbytes, prop_ms, peak, peak_kind, args.scale, prop_prec),
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},
         "gpu_launches": int(launches),
@@ -607,8 +610,11 @@ def main():
     ap.add_argument("--nci", choices=["procrustes", "printed"], default="procrustes",
                     help="T update of Algorithm 3 (the printed T = Phi^T Y collapses this "
                          "workload into one cluster)")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
-                    help="storage of the propagation's intermediate blocks (accumulation is FP32)")
+    ap.add_argument("--precision", choices=["fp32", "bf16-contract", "bf16-propagation", "bf16"],
+                    default="fp32",
+                    help="bf16-contract: products with R on the BF16 tensor cores; "
+                         "bf16-propagation: W and Z stored in BF16 between the SpMMs; bf16: both "
+                         "(accumulation is FP32 throughout)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
