@@ -630,71 +630,116 @@ int small_atb(int nseg, int m, const int* segk, int kmax, const double* A, int64
 }
 
 // ---------------------------------------------------------------------------
-// Per-chunk cluster sums S[l][m] = sum_{i in chunk, label i = l} X[i, m] and counts (one
-// thread per column, rows in order: deterministic). Labels outside [0, kmax) are skipped.
+// Per-chunk cluster sums S[l][m] = sum_{i in chunk, label i = l} X[i, m] and counts.
+// The chunk's rows are first bucketed by label with a stable counting sort in shared
+// memory; then each warp owns whole clusters and sums their rows in increasing row order
+// into registers (a float4 of columns per lane, 128 columns per CTA column tile). Every
+// sum is the row-ordered FP32 sum starting from 0, so the result does not depend on the
+// launch shape. Labels outside [0, kmax) are skipped.
 // ---------------------------------------------------------------------------
-__global__ void k_cluster_sums(const int64_t* __restrict__ chunk_row0,
-                               const int* __restrict__ chunk_rows, int kmax, int w,
-                               const float* __restrict__ X, int64_t ldx,
-                               const int32_t* __restrict__ labels, int col0, int wtile,
-                               float* __restrict__ part) {
-  extern __shared__ float accs[];  // [kmax][wtile] + counts[kmax]
+constexpr int kCsWarps = 8;
+constexpr int kCsCols = 128;  // columns per CTA (32 lanes x 4)
+
+__global__ void __launch_bounds__(kCsWarps * 32) k_cluster_sums(
+    const int64_t* __restrict__ chunk_row0, const int* __restrict__ chunk_rows, int kmax, int w,
+    const float* __restrict__ X, int64_t ldx, const int32_t* __restrict__ labels,
+    float* __restrict__ part) {
+  extern __shared__ int cs_smem[];
+  int* cnt = cs_smem;      // [kmax] rows per label
+  int* off = cnt + kmax;   // [kmax] bucket starts, then (after the scatter) bucket ends
+  int* idx = off + kmax;   // [rows] chunk-local row ids, bucketed by label, stable
   const int64_t c = blockIdx.x;
-  const int64_t r0 = chunk_row0[c], r1 = r0 + chunk_rows[c];
-  float* cnt = accs + (int64_t)kmax * wtile;
-  for (int q = threadIdx.x; q < kmax * wtile + kmax; q += blockDim.x) accs[q] = 0.f;
+  const int col0 = blockIdx.y * kCsCols;
+  const int64_t r0 = chunk_row0[c];
+  const int rows = chunk_rows[c];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int l = threadIdx.x; l < kmax; l += blockDim.x) cnt[l] = 0;
   __syncthreads();
-  const int m = threadIdx.x;
-  const int gm = col0 + m;
-  const bool active = m < wtile && gm < w;
-  const bool counter = threadIdx.x == 0 && col0 == 0;
-  constexpr int U = 32;  // rows whose loads are in flight together (adds stay in row order)
-  int64_t r = r0;
-  for (; r + U <= r1; r += U) {
-    int l[U];
-    float v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      l[u] = labels[r + u];
-      v[u] = active ? X[(r + u) * ldx + gm] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if ((unsigned)l[u] >= (unsigned)kmax) continue;
-      if (active) accs[l[u] * wtile + m] += v[u];
-      if (counter) cnt[l[u]] += 1.f;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const int l = labels[r0 + i];
+    if ((unsigned)l < (unsigned)kmax) atomicAdd(cnt + l, 1);  // counts: order-free
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int l = 0; l < kmax; ++l) {
+      off[l] = run;
+      run += cnt[l];
     }
   }
-  for (; r < r1; ++r) {
-    const int l = labels[r];
-    if ((unsigned)l >= (unsigned)kmax) continue;
-    if (active) accs[l * wtile + m] += X[r * ldx + gm];
-    if (counter) cnt[l] += 1.f;
+  __syncthreads();
+  if (warp == 0) {  // stable scatter: rows in order, 32 at a time, ranks by lane
+    for (int base = 0; base < rows; base += 32) {
+      const int i = base + lane;
+      const int l = i < rows ? labels[r0 + i] : -1;
+      const bool ok = (unsigned)l < (unsigned)kmax;
+      const unsigned peers = __match_any_sync(0xffffffffu, ok ? l : -1);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      const int pos = ok ? off[l] + rank : 0;
+      __syncwarp();
+      if (ok) {
+        idx[pos] = i;
+        if (rank == 0) off[l] += __popc(peers);
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   const int64_t width = (int64_t)kmax * w + kmax;
   float* out = part + c * width;
-  if (active)
-    for (int l = 0; l < kmax; ++l) out[(int64_t)l * w + gm] = accs[l * wtile + m];
-  if (col0 == 0)
-    for (int l = threadIdx.x; l < kmax; l += blockDim.x) out[(int64_t)kmax * w + l] = cnt[l];
+  const int cc = col0 + 4 * lane;
+  const bool act = cc < w;
+  const float* xc = X + (int64_t)r0 * ldx + cc;
+  for (int l = warp; l < kmax; l += kCsWarps) {
+    const int end = off[l], beg = end - cnt[l];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      int j = beg;
+      constexpr int U = 8;  // rows whose loads are in flight together
+      for (; j + U <= end; j += U) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_f4(xc + (int64_t)idx[j + u] * ldx);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          acc.x += v[u].x;
+          acc.y += v[u].y;
+          acc.z += v[u].z;
+          acc.w += v[u].w;
+        }
+      }
+      for (; j < end; ++j) {
+        const float4 v = ld_f4(xc + (int64_t)idx[j] * ldx);
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+      float* o = out + (int64_t)l * w + cc;
+      o[0] = acc.x;
+      if (cc + 1 < w) o[1] = acc.y;
+      if (cc + 2 < w) o[2] = acc.z;
+      if (cc + 3 < w) o[3] = acc.w;
+    }
+    if (blockIdx.y == 0 && lane == 0) out[(int64_t)kmax * w + l] = (float)cnt[l];
+  }
 }
 
 // S_s (layout [kmax][w] sums, then kmax counts) at S + s * (kmax*w + kmax)
 static int cluster_sums(const RowSpace& rs, const float* X, int w, int64_t ldx,
                         const int32_t* labels, int kmax, double* S, cudaStream_t s) {
+  ABG_CHECK(ldx % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0,
+            "cluster sums: rows must be 16-byte aligned");
   Scratch scr(s);
-  const int wtile = std::min(w, 256);
   const int64_t width = (int64_t)kmax * w + kmax;
   float* part;
   ABG_TRY(scr.get(&part, (size_t)std::max<int64_t>(1, rs.n_chunks) * width));
-  const size_t smem = sizeof(float) * ((size_t)kmax * wtile + kmax);
-  ABG_TRY(raise_smem_limit((const void*)k_cluster_sums, smem));
-  const int threads = (int)round_up(wtile, 32);
-  for (int col0 = 0; col0 < w; col0 += wtile) {
-    if (!rs.n_chunks) break;
-    k_cluster_sums<<<(unsigned)rs.n_chunks, threads, smem, s>>>(
-        rs.chunk_row0, rs.chunk_rows, kmax, w, X, ldx, labels, col0, wtile, part);
+  const size_t smem = sizeof(int) * (2 * (size_t)kmax + kChunk);
+  if (rs.n_chunks) {
+    ABG_TRY(raise_smem_limit((const void*)k_cluster_sums, smem));
+    dim3 grid((unsigned)rs.n_chunks, (unsigned)ceil_div(w, kCsCols));
+    k_cluster_sums<<<grid, kCsWarps * 32, smem, s>>>(rs.chunk_row0, rs.chunk_rows, kmax, w, X,
+                                                     ldx, labels, part);
     note_launch();
   }
   ABG_LAUNCH_CHECK();

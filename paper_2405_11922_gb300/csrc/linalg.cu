@@ -396,8 +396,8 @@ int cholqr2(const RowSpace& rs, const int* segl, int lmax, float* Y, int64_t ldy
 // One-sided (Hestenes) Jacobi SVD in FP32, one CTA per segment: the columns of
 // W_s = Bt_s (m x l_s, FP64 input, row stride lmax inside an m*lmax slab) are
 // rotated in round-robin order (the l/2 rotations of a step touch disjoint
-// column pairs, one warp per pair) until every pair is orthogonal to ~1e-6 of
-// its norms; then sigma_j = |w_j| and V holds the accumulated rotations, the
+// column pairs, a group of lanes per pair) until every pair is orthogonal to
+// max(1e-6, 4 sqrt(m) u) of its norms (u = 2^-24); then sigma_j = |w_j| and V holds the accumulated rotations, the
 // right singular vectors of Bt_s = the eigenvectors of Bt_s^T Bt_s. FP32 keeps
 // the error of sigma_j near 1e-7 sigma_1, the accuracy of the FP32 products
 // that formed Bt_s, at a fraction of the cost of FP64 on this GPU.
@@ -454,6 +454,10 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
   __syncthreads();
   const int mp = (l + 1) & ~1;  // even player count; index l is a bye when l is odd
   const int P = mp / 2;
+  // a pair counts as orthogonal below 4 sqrt(m) FP32 ulps of its norms (the rounding level of
+  // an m-term FP32 dot product; a fixed 1e-6 sits at that level for m ~ 100 and can keep the
+  // sweeps going to max_sweeps), and never above 1e-6 is required
+  const float tol = fmaxf(1e-6f, 4.f * sqrtf((float)m) * 5.9604645e-8f);
   // G lanes per column pair, so that one pass of the CTA's groups covers a step's P pairs
   // where it can (G >= 8 keeps the column loops a few elements deep per lane)
   const int G = P <= nw ? 32 : (P <= 2 * nw ? 16 : 8);
@@ -467,7 +471,12 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
       // see all 32 lanes; groups without a pair carry zeros and rotate nothing
       for (int i0 = warp * gpw; i0 < P; i0 += nw * gpw) {
         const int i = i0 + gi;
-        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (mp - 1)) + 1; };
+        auto player = [&](int pos) {  // round-robin seat pos at this step (seat 0 stays)
+          if (pos == 0) return 0;
+          int x = pos - 1 + step;       // < 2 (mp - 1)
+          if (x >= mp - 1) x -= mp - 1;
+          return x + 1;
+        };
         int pc = 0, qc = l;
         if (i < P) {
           const int a = player(i), b = player(mp - 1 - i);
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
           be += __shfl_xor_sync(0xffffffffu, be, o, G);
           ga += __shfl_xor_sync(0xffffffffu, ga, o, G);
         }
-        if (!valid || !(fabsf(ga) > 1e-6f * sqrtf(al * be))) continue;  // uniform over the group
+        if (!valid || !(fabsf(ga) > tol * sqrtf(al * be))) continue;  // uniform over the group
         const float zeta = (be - al) / (2.f * ga);
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float c = rsqrtf(fmaf(t, t, 1.f));
