@@ -415,6 +415,7 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
                                                        float* __restrict__ warm, int warm_in) {
   extern __shared__ float sv_smem[];
   __shared__ int s_rot;
+  __shared__ unsigned s_maxr;  // largest |cos| between a pair's columns this sweep (float bits)
   const int sg = blockIdx.x;
   const int l = segl[sg];
   const double* Bt = Btall + (int64_t)sg * m * lmax;
@@ -463,9 +464,13 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
   const int G = P <= nw ? 32 : (P <= 2 * nw ? 16 : 8);
   const int gpw = 32 / G, gi = lane / G, gl = lane % G;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_maxr = 0u;
+    }
     __syncthreads();
     int rotated = 0;
+    float maxr = 0.f;
     for (int step = 0; step < mp - 1; ++step) {
       // i0 is uniform over the warp, so every lane runs the same trips and the shuffles below
       // see all 32 lanes; groups without a pair carry zeros and rotate nothing
@@ -500,8 +505,11 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
           ga += __shfl_xor_sync(0xffffffffu, ga, o, G);
         }
         if (!valid || !(fabsf(ga) > tol * sqrtf(al * be))) continue;  // uniform over the group
-        const float zeta = (be - al) / (2.f * ga);
-        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        maxr = fmaxf(maxr, fabsf(ga) * rsqrtf(al * be));
+        // the angle only needs to be close: c and s below stay a rotation to rounding
+        const float zeta = __fdividef(be - al, 2.f * ga);
+        const float t = __fdividef(zeta >= 0.f ? 1.f : -1.f,
+                                   fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float c = rsqrtf(fmaf(t, t, 1.f));
         const float sn = c * t;
         for (int r = gl; r < m; r += G) {
@@ -521,10 +529,17 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
       __syncthreads();
     }
     rotated = __any_sync(0xffffffffu, rotated);
-    if (rotated && lane == 0) atomicOr(&s_rot, 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxr = fmaxf(maxr, __shfl_xor_sync(0xffffffffu, maxr, o));
+    if (lane == 0) {
+      if (rotated) atomicOr(&s_rot, 1);
+      atomicMax(&s_maxr, __float_as_uint(maxr));  // non-negative floats order as integers
+    }
     __syncthreads();
-    const bool done = s_rot == 0;
-    __syncthreads();  // every thread has read the flag before thread 0 resets it
+    // done when no pair rotated, or when the largest rotated pair was below sqrt(tol)/4:
+    // the sweeps converge quadratically, so the next one would find every pair below tol
+    const bool done = s_rot == 0 || __uint_as_float(s_maxr) < 0.25f * sqrtf(tol);
+    __syncthreads();  // every thread has read the flags before thread 0 resets them
     if (done) break;
   }
   // sigma_j^2 = |w_j|^2 (one warp per column), then rank descending (ties by index)
