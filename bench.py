@@ -310,6 +310,33 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clocks = sampler.summary()
     prop_ms = statistics.median(r.ms_phase[1] for r in results)
     phase_ms = [statistics.median(r.ms_phase[i] for r in results) for i in range(6)]
+    quality = quality_of(g, labels, results[-1])
+    variant = None
+    if args.precision == "fp32" and rank == 0 and not args.no_variant:
+        # the same solve with the BF16 options (products with R in BF16 on the tensor cores,
+        # W / Z stored in BF16 between the SpMMs), on the same resident graph
+        ref_labels = labels.copy()
+        pv = abg.params(**PARAMS, procrustes=args.nci == "procrustes", bf16_propagation=True,
+                        bf16_contract=True)
+        abg.abg_cluster(graph, pv, labels, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vres = [abg.abg_cluster(graph, pv, labels, stream)[1] for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / args.steps
+        variant = {"precision": "bf16 (bf16-contract + bf16-propagation)",
+                   "value": 1e3 / vms, "unit": "solves/s", "ms_per_step": vms,
+                   "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf",
+                                         "nci", "objective"],
+                                        [statistics.median(r.ms_phase[i] for r in vres)
+                                         for i in range(6)])),
+                   "quality": quality_of(g, labels, vres[-1]),
+                   "labels_equal_to_fp32": float(np.mean(labels == ref_labels)),
+                   "objective_rel_diff_vs_fp32":
+                       vres[-1].objective / results[-1].objective - 1.0}
+        labels[:] = ref_labels
     graph.close()
 
     # ---- end to end through the C ABI from pinned host memory ----
@@ -358,9 +385,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": pin.h2d_bytes, "d2h_bytes_per_step": int(labels.nbytes)},
         "gpu_launches": int(launches),
-        "quality": quality_of(g, labels, results[-1]),
+        "quality": quality,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    if variant is not None:
+        line["bf16_variant"] = variant
     if world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
         line["cpu_baseline"] = {"value": 1.0 / r["seconds_full_est"], "unit": "solves/s",
@@ -598,6 +627,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the BF16 variant timed after the FP32 steps")
     ap.add_argument("--workload", choices=["large", "batched", "serve", "config1", "config2"],
                     default="large")
     ap.add_argument("--graphs", type=int, default=512, help="batched workload: number of graphs")
