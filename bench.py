@@ -591,7 +591,8 @@ def run_small_config(args):
         pdict = dict(k=20, alpha=0.6, gamma=6, d=128, t_f=5, t_g=20, seed=0)
         label = ("planted ABG |U|=200k |V|=500k, 5M edge draws (Zipf 2.1), TF-IDF-like sparse "
                  "attributes d_u=1000 reduced to d=128, k=20, alpha=0.6, gamma=6, T_f=5, T_g=20")
-    p = abg.params(**pdict)
+    p = abg.params(**pdict, bf16_propagation=args.precision in ("bf16-propagation", "bf16"),
+                   bf16_contract=args.precision in ("bf16-contract", "bf16"))
     stream = torch.cuda.current_stream()
     h = abg.abg_create(g, stream=stream)
     for _ in range(args.warmup):
@@ -610,9 +611,11 @@ def run_small_config(args):
     line = {"metric": "TPO solves/s and propagation rounds/s on one planted ABG",
             "value": args.steps / el, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f32+bf16",
             "data": "synthetic", "config": {"workload": label, "n_u": int(g.n_u),
-                                            "n_v": int(g.n_v), "nnz": int(g.nnz)},
+                                            "n_v": int(g.n_v), "nnz": int(g.nnz),
+                                            "precision": args.precision},
             "prop_rounds_per_s": pdict["gamma"] / (phase[1] / 1e3),
             "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
                                   "objective"], phase))}

@@ -105,7 +105,7 @@ int gaussian_f32(int nseg, const uint64_t* seeds, int stream_id, int rows, int c
 
 // ---------------------------------------------------------------------------
 // One CTA per segment: Cholesky G_s = R^T R (R upper, positive diagonal) and
-// R^-1 in FP64 (shared memory when both triangles fit). A non-positive (or
+// R^-1 in FP64 (shared memory when both triangles fit; both are written out). A non-positive (or
 // relatively negligible) pivot zeroes that row of R and that column of R^-1
 // (the column of Q it would produce is dropped) and is counted in *breakdowns.
 // Slabs: G_s at G + s*gseg (row stride ldg); R_s, Ri_s at R + s*l*l with l the
@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl,
   __syncthreads();
   for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
     const double v = Ri[q];
-    if (in_smem) Rig[q] = v;
+    if (in_smem) {
+      Rig[q] = v;
+      Rg[q] = R[q];
+    }
     if (ri32) ri32[(q / l) * ldr32 + (q % l)] = (float)v;
   }
 }
@@ -570,12 +573,50 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
     for (int64_t q = tid; q < (int64_t)l * l; q += nt) V0[q] = V[q];
 }
 
+// Rt_s (lmax x lmax, row stride lmax) = R_s (l_s x l_s, row stride l_s), zeros elsewhere
+__global__ void k_pad_square(const int* __restrict__ segl, int lmax, const double* __restrict__ R,
+                             double* __restrict__ Rt) {
+  const int sg = blockIdx.y;
+  const int l = segl[sg];
+  const int64_t o = (int64_t)sg * lmax * lmax;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)lmax * lmax;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / lmax), j = (int)(q % lmax);
+    Rt[o + q] = (i < l && j < l) ? R[o + (int64_t)i * l + j] : 0.0;
+  }
+}
+
 int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
               double* evecs, cudaStream_t s, float* warm, bool warm_valid) {
   ABG_CHECK(lmax <= kMaxRsvdBlock, "svd: block width above %d", kMaxRsvdBlock);
   Scratch scr(s);
   const size_t smem = sizeof(float) * ((size_t)m * lmax + (size_t)lmax * lmax);
   const int in_smem = smem <= 200 * 1024;
+  const size_t smem_sq = sizeof(float) * 2 * (size_t)lmax * lmax;
+  if (!in_smem && m > lmax && smem_sq <= 200 * 1024 && segl) {
+    // Tall B^T (m x l) = Q R with R the Cholesky factor of the FP64 Gram B^T^T B^T: R has the
+    // same right singular vectors and singular values, and its l x l Jacobi runs in shared
+    // memory instead of sweeping m-long columns in global memory
+    const int64_t l2 = (int64_t)lmax * lmax;
+    double *gram, *R, *Ri, *Rt;
+    int* bd;
+    ABG_TRY(scr.get(&gram, (size_t)nseg * l2));
+    ABG_TRY(scr.get(&R, (size_t)nseg * l2));
+    ABG_TRY(scr.get(&Ri, (size_t)nseg * l2));
+    ABG_TRY(scr.get(&Rt, (size_t)nseg * l2));
+    ABG_TRY(scr.get(&bd, 1));
+    ABG_CUDA(cudaMemsetAsync(bd, 0, sizeof(int), s));
+    dim3 grid((unsigned)ceil_div(l2, 128), (unsigned)nseg);
+    k_small_tn64<<<grid, 128, 0, s>>>(m, segl, lmax, segl, lmax, Bt, lmax, (int64_t)m * lmax, Bt,
+                                      lmax, (int64_t)m * lmax, gram, lmax, l2);
+    note_launch();
+    ABG_TRY(chol_inv(nseg, segl, lmax, gram, lmax, l2, R, Ri, l2, nullptr, 0, 0, bd, s));
+    dim3 g2((unsigned)std::min<int64_t>(ceil_div(l2, 256), 1024), (unsigned)nseg);
+    k_pad_square<<<g2, 256, 0, s>>>(segl, lmax, R, Rt);
+    note_launch();
+    ABG_LAUNCH_CHECK();
+    return svd_right(nseg, lmax, segl, lmax, Rt, evals, evecs, s, warm, warm_valid);
+  }
   float *W = nullptr, *V = nullptr;
   if (!in_smem) {
     ABG_TRY(scr.get(&W, (size_t)nseg * m * lmax));
