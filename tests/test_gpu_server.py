@@ -155,3 +155,24 @@ def test_resident_graph_resolves():
     b.close()
     tiny.close()
     h.close()
+
+
+def test_served_mixed_precisions_equal_alone():
+    # requests asking for the BF16 options are batched only with requests asking for the same
+    # precision, and each result equals the request solved alone
+    reqs = []
+    for i in range(9):
+        n_u = [300, 2500, 900][i % 3]
+        g = synth.make_small(700 + i, n_u=n_u, n_v=int(1.5 * n_u), k=4, d_u=24, deg=6,
+                             signal=3.0)
+        p = abg.params(k=4, alpha=0.6, gamma=4, t_f=4, t_g=8, seed=2000 + i,
+                       bf16_contract=i % 3 == 1, bf16_propagation=i % 3 == 2)
+        reqs.append((g, p))
+    sv = abg.Server(workers=2, max_batch_graphs=8)
+    rids = [sv.submit(g, p) for g, p in reqs]
+    for (g, p), rid in zip(reqs, rids):
+        st, lab, res = sv.poll(rid, 60_000_000)
+        assert st == abg.ABG_OK, abg.lib().abg_last_error().decode()
+        lab1, res1 = _alone(g, p)
+        assert np.array_equal(lab, lab1) and res.objective == res1.objective
+    sv.close()
