@@ -175,6 +175,10 @@ ABG_API int64_t abg_launch_count(void);
  * tall-skinny products run there unless the environment variable
  * ABG_TENSOR_CORES is set to 0 (then on the FP32 SIMT kernels). */
 ABG_API int64_t abg_tensor_core_launches(void);
+/* SpMM autotuner: product shapes measured so far in this process (the first product of a
+ * large enough shape times its kernel variants; the outputs are the same bits whichever
+ * variant runs). ABG_AUTOTUNE=0 in the environment turns the measuring off. */
+ABG_API int64_t abg_spmm_tuned_shapes(void);
 
 /* ---- graph lifetime ------------------------------------------------------ */
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "abg_params_default": (None, [_p]),
     "abg_launch_count": (_i64, []),
     "abg_tensor_core_launches": (_i64, []),
+    "abg_spmm_tuned_shapes": (_i64, []),
     "abg_create": (C.c_int, [_p, _p, _p]),
     "abg_destroy": (None, [_p]),
     "abg_graph_footprint": (_i64, [_p]),
@@ -262,6 +263,10 @@ def abg_launch_count() -> int:
 
 def abg_tensor_core_launches() -> int:
     return int(lib().abg_tensor_core_launches())
+
+
+def abg_spmm_tuned_shapes() -> int:
+    return int(lib().abg_spmm_tuned_shapes())
 
 
 def _desc_of(g, keep: list, side: int = ABG_SIDE_U) -> abg_graph_desc:

@@ -12,6 +12,11 @@
 // edges are split into kHeavyChunk-edge chunks whose partial sums go to a
 // scratch buffer and are added back in chunk order, so results do not depend
 // on scheduling (no floating-point atomics).
+#include <atomic>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -814,19 +819,31 @@ static int run_spmm_tma(const abg_graph::Schedule& sc, const int64_t* ptr, const
   return ABG_OK;
 }
 
+// Light-task variants of one product (rows of 17..64 float4 chunks, where all three apply):
+//   0  TMA gather4 ring (k_spmm_tma)          1  register gathers, one warp per task
+//   2  a lane group per row over all tasks (k_spmm_stream), heavy chunks by k_spmm_chunks
+// Every variant sums each row's edges in edge order, so they give the same bits.
+enum SpmmVariant { kVarTma = 0, kVarWarp = 1, kVarRows = 2 };
+
 template <int G, int V, class TIn>
-static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t n_rows,
-                    const int64_t* ptr, const int32_t* col, const float* val, const TIn* B,
-                    int64_t ldb, int64_t b_rows, float* C, int64_t ldc, int nchunk,
-                    const EpiParams& ep, float* part, int64_t ldp, int* wait_err, cudaStream_t s) {
-  bool tma = false;  // light tasks with edges and the heavy chunks are done
+static int run_variant(int vid, bool* ran, const abg_graph::Schedule* sc, const int32_t* rows,
+                       int64_t n_rows, const int64_t* ptr, const int32_t* col, const float* val,
+                       const TIn* B, int64_t ldb, int64_t b_rows, float* C, int64_t ldc,
+                       int nchunk, const EpiParams& ep, float* part, int64_t ldp, int* wait_err,
+                       cudaStream_t s) {
+  *ran = true;
+  bool light = false;  // light tasks with edges and the heavy chunks are done
   if constexpr (G == 32 && V <= 2) {
-    if (sc) {
+    if (sc && vid == kVarTma) {
       const int st = run_spmm_tma<V, TIn>(*sc, ptr, col, val, B, ldb, b_rows, C, ldc, nchunk, ep,
-                                          part, ldp, wait_err, s, &tma);
+                                          part, ldp, wait_err, s, &light);
       if (st != ABG_OK) return st;
+      if (!light) {  // the TMA path declined this shape
+        *ran = false;
+        return ABG_OK;
+      }
     }
-    if (sc && !tma) {  // the TMA path declined this shape: register gathers, one warp per item
+    if (sc && vid == kVarWarp) {  // register gathers, one warp per item
       constexpr int U = ABG_WARP_UNR, MB = ABG_WARP_MINB;
       const SpmmItems items{sc->etasks, sc->chunk_begin, sc->chunk_row_slot, sc->heavy_row};
       if (sc->n_chunks > 0) {
@@ -848,10 +865,10 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
               items, sc->n_etasks, ptr, col, val, B, (int)ldb, C, (int)ldc, nchunk, ep);
         ::abg::note_launch();
       }
-      tma = true;
+      light = true;
     }
   }
-  if (tma) {
+  if (light) {
     if (sc->n_ztasks > 0) {
       k_spmm_stream<G, V, TIn><<<blocks_for(sc->n_ztasks, G), 256, 0, s>>>(
           sc->ztasks, sc->n_ztasks, ptr, col, val, B, ldb, C, ldc, nchunk, ep); ::abg::note_launch();
@@ -864,7 +881,7 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
                                                                  ldb, C, ldc, nchunk, ep); ::abg::note_launch();
   }
   if (sc && sc->n_chunks > 0) {
-    if (!tma) {
+    if (!light) {
       k_spmm_chunks<G, V, TIn><<<blocks_for(sc->n_chunks, G), 256, 0, s>>>(
           sc->chunk_begin, sc->chunk_row_slot, sc->heavy_row, sc->n_chunks, ptr, col, val, B, ldb,
           part, ldp, nchunk); ::abg::note_launch();
@@ -874,6 +891,96 @@ static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t 
   }
   ABG_LAUNCH_CHECK();
   return ABG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SpMM autotuner: the first product of a shape (the schedule's task, edge-task and chunk
+// counts, the row width and the operand type) runs every variant twice and times the second
+// run with CUDA events on its stream; later products of that shape, in this graph or another
+// one of the same structure (the same graph uploaded again), use the fastest. The outputs are
+// the same bits whichever variant runs, so the choice only moves time. Products with fewer
+// than kTuneMinItems tasks and chunks (where the measuring would cost more than it can save)
+// and ABG_AUTOTUNE=0 in the environment keep the fixed order (TMA ring, else register
+// gathers).
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+  int64_t n_tasks, n_etasks, n_chunks;
+  int nchunk, tsize;
+  bool operator<(const TuneKey& o) const {
+    if (n_tasks != o.n_tasks) return n_tasks < o.n_tasks;
+    if (n_etasks != o.n_etasks) return n_etasks < o.n_etasks;
+    if (n_chunks != o.n_chunks) return n_chunks < o.n_chunks;
+    if (nchunk != o.nchunk) return nchunk < o.nchunk;
+    return tsize < o.tsize;
+  }
+};
+constexpr size_t kTuneCap = 4096;  // shapes remembered (the table is cleared beyond this)
+constexpr int64_t kTuneMinItems = 1 << 15;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+std::atomic<int64_t> g_tuned{0};  // shapes measured
+
+bool autotune_enabled() {
+  const char* e = std::getenv("ABG_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+}  // namespace
+
+template <int G, int V, class TIn>
+static int run_spmm(const abg_graph::Schedule* sc, const int32_t* rows, int64_t n_rows,
+                    const int64_t* ptr, const int32_t* col, const float* val, const TIn* B,
+                    int64_t ldb, int64_t b_rows, float* C, int64_t ldc, int nchunk,
+                    const EpiParams& ep, float* part, int64_t ldp, int* wait_err, cudaStream_t s) {
+  bool ran = false;
+  auto run = [&](int vid) {
+    return run_variant<G, V, TIn>(vid, &ran, sc, rows, n_rows, ptr, col, val, B, ldb, b_rows, C,
+                                  ldc, nchunk, ep, part, ldp, wait_err, s);
+  };
+  if constexpr (G == 32 && V <= 2) {
+    if (sc && sc->n_etasks + sc->n_chunks > 0) {
+      if (!autotune_enabled() || sc->n_etasks + sc->n_chunks < kTuneMinItems) {
+        ABG_TRY(run(kVarTma));
+        return ran ? ABG_OK : run(kVarWarp);
+      }
+      const TuneKey key{sc->n_tasks, sc->n_etasks, sc->n_chunks, nchunk, (int)sizeof(TIn)};
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      const auto it = g_tune.find(key);
+      if (it != g_tune.end()) return run(it->second);
+      cudaEvent_t e0, e1;
+      ABG_CUDA(cudaEventCreate(&e0));
+      ABG_CUDA(cudaEventCreate(&e1));
+      int best = kVarWarp;
+      float best_ms = INFINITY;
+      int st = ABG_OK;
+      for (int vid : {kVarTma, kVarWarp, kVarRows}) {
+        if ((st = run(vid)) != ABG_OK) break;  // warm-up run (and: does the variant apply?)
+        if (!ran) continue;
+        cudaEventRecord(e0, s);
+        if ((st = run(vid)) != ABG_OK) break;
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) !=
+                                                           cudaSuccess) {
+          st = ABG_EDEVICE;
+          set_error("SpMM autotuner: timing failed");
+          break;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = vid;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (st != ABG_OK) return st;
+      if (g_tune.size() >= kTuneCap) g_tune.clear();
+      g_tune[key] = best;
+      g_tuned.fetch_add(1);
+      return run(best);  // the output of the chosen variant (the same bits as any other)
+    }
+  }
+  return run(kVarRows);
 }
 
 template <class TIn>
@@ -1061,3 +1168,5 @@ int f32_to_bf16(const float* x, int64_t ldx, int64_t rows, int cols, __nv_bfloat
 }
 
 }  // namespace abg
+
+extern "C" ABG_API int64_t abg_spmm_tuned_shapes(void) { return abg::g_tuned.load(); }
