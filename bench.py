@@ -174,6 +174,23 @@ def roofline_of(pbytes: float, prop_ms: float, peak: float, peak_kind: str, scal
     return out
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's); x itself when not
+    distributed. device: where the collective's tensor lives ("cuda" for NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, elapsed_max_s: float) -> float:
+    """Whole-job solves/s: every rank solves `steps` graphs; the job takes the slowest rank's
+    time."""
+    return world * steps / elapsed_max_s
+
+
 def csc_of(g):
     order = np.argsort(g.v_idx, kind="stable")
     v_ptr = np.zeros(g.n_v + 1, dtype=np.int64)
@@ -303,10 +320,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         barrier()
     launches = abg.abg_launch_count() - l0
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     clocks = sampler.summary()
     prop_ms = statistics.median(r.ms_phase[1] for r in results)
     phase_ms = [statistics.median(r.ms_phase[i] for r in results) for i in range(6)]
@@ -354,10 +368,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         gh.close()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
     if rank != 0:
         return
@@ -365,7 +376,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     prop_prec = "bf16" if args.precision in ("bf16-propagation", "bf16") else "fp32"
     pbytes = propagation_bytes(g, PARAMS["d"], PARAMS["gamma"], prop_prec)
     achieved = pbytes / (prop_ms / 1e3) / 1e9
-    value = world * args.steps / elapsed
+    value = job_value(world, args.steps, elapsed)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
