@@ -479,9 +479,18 @@ __global__ void k_colsum_part(const int64_t* __restrict__ chunk_row0,
                               double* __restrict__ part) {
   const int64_t c = blockIdx.x;
   const int64_t r0 = chunk_row0[c], r1 = r0 + chunk_rows[c];
+  constexpr int U = 16;  // rows whose loads are in flight together (the adds stay in row order)
   for (int n = threadIdx.x; n < N; n += blockDim.x) {
     double s = 0.0;
-    for (int64_t r = r0; r < r1; ++r) s += (double)A[r * lda + n];
+    int64_t r = r0;
+    for (; r + U <= r1; r += U) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = A[(r + u) * lda + n];
+#pragma unroll
+      for (int u = 0; u < U; ++u) s += (double)v[u];
+    }
+    for (; r < r1; ++r) s += (double)A[r * lda + n];
     part[c * N + n] = s;
   }
 }
@@ -503,7 +512,9 @@ int column_sums(const RowSpace& rs, int N, const float* A, int64_t lda, double* 
 // ---------------------------------------------------------------------------
 // Random features (Eqs. 13-14)
 // ---------------------------------------------------------------------------
-// R[i] <- R'[i] / sqrt(max(R'[i].r_s, 1e-300)) with s the row's segment; one warp per row.
+// R[i] <- R'[i] / sqrt(max(R'[i].r_s, 1e-300)) with s the row's segment; one warp per row,
+// the row held in registers (PER values per lane, all loads in flight together).
+template <int PER>
 __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t ldr,
                                const double* __restrict__ r, const int* __restrict__ row_seg,
                                int* __restrict__ clamped, __nv_bfloat16* __restrict__ R16,
@@ -513,16 +524,29 @@ __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t
   if (row >= n) return;
   const double* rsg = r + (int64_t)row_seg[row] * w2;
   float* rp = R + row * ldr;
+  float x[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int c = lane + 32 * i;
+    x[i] = c < w2 ? rp[c] : 0.f;
+  }
   float part = 0.f;
-  for (int c = lane; c < w2; c += 32) part = fmaf(rp[c], (float)rsg[c], part);
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int c = lane + 32 * i;
+    if (c < w2) part = fmaf(x[i], (float)rsg[c], part);
+  }
   double dot = (double)part;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   const bool clamp = !(dot > 1e-300);
   if (clamp) dot = 1e-300;
   const float inv = (float)(1.0 / sqrt(dot));
-  for (int c = lane; c < w2; c += 32) {
-    const float v = rp[c] * inv;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int c = lane + 32 * i;
+    if (c >= w2) continue;
+    const float v = x[i] * inv;
     rp[c] = v;
     if (R16) R16[row * ldr16 + c] = __float2bfloat16_rn(v);
   }
@@ -554,9 +578,18 @@ int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, c
   ABG_TRY(scr.get(&r, (size_t)rs.nseg * 2 * d));
   ABG_TRY(reduce_pieces<double>(rs, true, cpart, 2 * d, 2 * d, nullptr, 1, nullptr, 2 * d, r,
                                 2 * d, 2 * d, s));
-  k_rf_normalise<<<(unsigned)ceil_div(rs.rows, 8), 256, 0, s>>>(rs.rows, 2 * d, R, ldr, r,
-                                                                 rs.row_seg, clamped_dev, R16,
-                                                                 ldr16);
+  const unsigned grid = (unsigned)ceil_div(rs.rows, 8);
+  const int w2 = 2 * d;
+#define ABG_RF_CASE(per)                                                                 \
+  if (w2 <= 32 * per) {                                                                  \
+    k_rf_normalise<per><<<grid, 256, 0, s>>>(rs.rows, w2, R, ldr, r, rs.row_seg, clamped_dev, \
+                                             R16, ldr16);                                \
+  } else
+  ABG_RF_CASE(2) ABG_RF_CASE(4) ABG_RF_CASE(8) ABG_RF_CASE(16) ABG_RF_CASE(32) ABG_RF_CASE(64) {
+    set_error("random features: 2d above 2048");
+    return ABG_EINVAL;
+  }
+#undef ABG_RF_CASE
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;
