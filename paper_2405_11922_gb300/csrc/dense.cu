@@ -69,25 +69,6 @@ __device__ __forceinline__ Best merge_best(Best a, Best b) {
 // threads, thread tile 8 rows x TN columns (columns (tx + 16 j) * 4 .. +4 for
 // TN >= 4). EPI: 0 element-wise, 1 sin/cos + column sums, 2 row argmax.
 // ---------------------------------------------------------------------------
-// sin and cos of x for |x| up to a few hundred (Eq. 13 feeds |x| <= sqrt(d)): x = k pi/2 + r
-// with |r| <= pi/4 by a two-part Cody-Waite reduction (pi/2 split into its float value and
-// the remainder, each product fused), then the hardware approximations on r, whose absolute
-// error stays below 2^-21 on [-pi, pi], and the quadrant k mod 4. The reduced argument carries
-// one float rounding (at most 2^-25 for |r| <= pi/4; the constants' own error times |k| is far
-// smaller), so the result keeps the 2^-21 absolute accuracy of the approximations.
-__device__ __forceinline__ void sincos_rr(float x, float* s, float* c) {
-  const float k = rintf(x * 0.636619772f);        // 2 / pi
-  float r = fmaf(-k, 1.57079637f, x);             // float(pi / 2)
-  r = fmaf(-k, -4.37113900e-8f, r);               // pi / 2 - float(pi / 2)
-  const float sr = __sinf(r), cr = __cosf(r);
-  switch ((int)k & 3) {                           // sin, cos of r + q pi / 2
-    case 0: *s = sr; *c = cr; break;
-    case 1: *s = cr; *c = -sr; break;
-    case 2: *s = -sr; *c = -cr; break;
-    default: *s = -cr; *c = sr; break;
-  }
-}
-
 template <int TN, int EPI>
 __global__ void __launch_bounds__(256) k_gemm_nn(NNK p) {
   constexpr int BM = 128, BK = 16, BN = 16 * TN, TM = 8;
@@ -190,7 +171,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(NNK p) {
         const int gn = col_of(j);
         if (gn >= N) continue;
         float sv, cv;
-        sincos_rr(p.in_scale * acc[i][j], &sv, &cv);
+        sincosf(p.in_scale * acc[i][j], &sv, &cv);
         sv *= p.out_scale;
         cv *= p.out_scale;
         p.C[gm * p.ldc + gn] = sv;
