@@ -160,3 +160,17 @@ def test_nci_procrustes_scores_and_fixed_point():
     lab3, T3, _, ch3 = tpo.nci(Phi, 12, early_stop=True)
     lab4, T4, _, _ = tpo.nci(Phi, 12)
     assert np.array_equal(lab3, lab4) and np.allclose(T3, T4, atol=1e-12) and len(ch3) <= 12
+
+
+def test_printed_t_collapses_many_clusters_procrustes_keeps_them():
+    # the large workload's generator at 1% (20,000 U nodes, k = 100): with T = Phi^T Y as
+    # printed every score Phi[i].T[:, l] = sum_{j in C_l} Phi[i].Phi[j] / sqrt(|C_l|) is positive
+    # and grows with the cluster, so one cluster absorbs the rest; the orthogonal Procrustes T
+    # (the constraint T T^T = I of Eq. 20) keeps the clusters apart
+    g = synth.make_config3(scale=0.01)
+    p = dict(k=100, alpha=0.9, gamma=10, d=128, t_f=5, t_g=20, seed=0)
+    printed = tpo.tpo(g, **p)
+    assert np.unique(printed["labels"]).size == 1 and printed["objective"] == 0.0
+    proc = tpo.tpo(g, procrustes=True, **p)
+    assert np.unique(proc["labels"]).size >= 90
+    assert metrics.nmi(g.truth, proc["labels"]) >= 0.4
