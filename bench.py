@@ -191,6 +191,42 @@ def job_value(world: int, steps: int, elapsed_max_s: float) -> float:
     return world * steps / elapsed_max_s
 
 
+VARIANTS = (("bf16_contract_variant", "bf16-contract (SpMM FP32, products with R in BF16)",
+             dict(bf16_contract=True)),
+            ("bf16_variant", "bf16 (bf16-contract + bf16-propagation)",
+             dict(bf16_contract=True, bf16_propagation=True)))
+
+
+def time_variants(abg, torch, graph, g, labels, results, stream, args) -> dict:
+    """Time the BF16 variants of the FP32 solve on its resident graph (one untimed solve, then
+    args.steps timed with CUDA events) and compare them with the FP32 result held in
+    `labels` / `results`; `labels` holds the FP32 labels again on return."""
+    ref_labels = labels.copy()
+    out = {}
+    for key, desc, flags in VARIANTS:
+        pv = abg.params(**PARAMS, procrustes=args.nci == "procrustes", **flags)
+        abg.abg_cluster(graph, pv, labels, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vres = [abg.abg_cluster(graph, pv, labels, stream)[1] for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / args.steps
+        out[key] = {"precision": desc, "value": 1e3 / vms, "unit": "solves/s",
+                    "ms_per_step": vms,
+                    "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf",
+                                          "nci", "objective"],
+                                         [statistics.median(r.ms_phase[i] for r in vres)
+                                          for i in range(6)])),
+                    "quality": quality_of(g, labels, vres[-1]),
+                    "labels_equal_to_fp32": float(np.mean(labels == ref_labels)),
+                    "objective_rel_diff_vs_fp32":
+                        vres[-1].objective / results[-1].objective - 1.0}
+    labels[:] = ref_labels
+    return out
+
+
 def csc_of(g):
     order = np.argsort(g.v_idx, kind="stable")
     v_ptr = np.zeros(g.n_v + 1, dtype=np.int64)
@@ -325,32 +361,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     prop_ms = statistics.median(r.ms_phase[1] for r in results)
     phase_ms = [statistics.median(r.ms_phase[i] for r in results) for i in range(6)]
     quality = quality_of(g, labels, results[-1])
-    variant = None
+    variants = {}
     if args.precision == "fp32" and rank == 0 and not args.no_variant:
-        # the same solve with the BF16 options (products with R in BF16 on the tensor cores,
-        # W / Z stored in BF16 between the SpMMs), on the same resident graph
-        ref_labels = labels.copy()
-        pv = abg.params(**PARAMS, procrustes=args.nci == "procrustes", bf16_propagation=True,
-                        bf16_contract=True)
-        abg.abg_cluster(graph, pv, labels, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        vres = [abg.abg_cluster(graph, pv, labels, stream)[1] for _ in range(args.steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        vms = e0.elapsed_time(e1) / args.steps
-        variant = {"precision": "bf16 (bf16-contract + bf16-propagation)",
-                   "value": 1e3 / vms, "unit": "solves/s", "ms_per_step": vms,
-                   "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf",
-                                         "nci", "objective"],
-                                        [statistics.median(r.ms_phase[i] for r in vres)
-                                         for i in range(6)])),
-                   "quality": quality_of(g, labels, vres[-1]),
-                   "labels_equal_to_fp32": float(np.mean(labels == ref_labels)),
-                   "objective_rel_diff_vs_fp32":
-                       vres[-1].objective / results[-1].objective - 1.0}
-        labels[:] = ref_labels
+        # the same solve with the BF16 options on the same resident graph: the products with R
+        # in BF16 on the tensor cores (SpMM in FP32), then also W / Z stored in BF16
+        variants = time_variants(abg, torch, graph, g, labels, results, stream, args)
     graph.close()
 
     # ---- end to end through the C ABI from pinned host memory ----
@@ -399,8 +414,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "quality": quality,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
-    if variant is not None:
-        line["bf16_variant"] = variant
+    line.update(variants)
     if world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
         line["cpu_baseline"] = {"value": 1.0 / r["seconds_full_est"], "unit": "solves/s",

@@ -34,3 +34,60 @@ def test_propagation_bytes_formula():
     bf16 = bench.propagation_bytes(g, d, gamma, "bf16")
     # BF16 storage halves the gathered W / Z rows and their writes, except the final Z
     assert fp32 / 2 < bf16 < fp32
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        _FakeCuda.clock += 10.0
+        self.t = _FakeCuda.clock
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class _FakeCuda:
+    clock = 0.0
+    Event = _FakeEvent
+
+    @staticmethod
+    def synchronize():
+        pass
+
+
+class _FakeRes:
+    def __init__(self, objective):
+        self.objective = objective
+        self.ms_phase = [0.0, 50.0, 8.0, 50.0, 36.0, 0.7]
+
+
+class _FakeAbg:
+    def params(self, **kw):
+        return kw
+
+    def abg_cluster(self, graph, p, labels, stream):
+        # the BF16 options move one label and the objective a little
+        labels[:] = np.arange(labels.size) % 4
+        if p.get("bf16_contract"):
+            labels[0] = 1
+        return labels, _FakeRes(2.0 + (1e-6 if p.get("bf16_propagation") else 0.0))
+
+
+def test_time_variants_reports_both_bf16_forms_and_restores_labels():
+    g = SimpleNamespace(truth=np.arange(40) % 4)
+    labels = np.arange(40) % 4
+    before = labels.copy()
+    args = SimpleNamespace(steps=5, nci="procrustes")
+    out = bench.time_variants(_FakeAbg(), SimpleNamespace(cuda=_FakeCuda), None, g, labels,
+                              [_FakeRes(2.0)], None, args)
+    assert set(out) == {"bf16_contract_variant", "bf16_variant"}
+    for v in out.values():
+        assert v["ms_per_step"] == 10.0 / 5 and v["value"] == 1e3 / 2.0
+        assert v["labels_equal_to_fp32"] == 39 / 40
+        assert v["quality"]["clusters_nonempty"] == 4
+        assert v["phase_ms"]["propagation"] == 50.0
+    assert out["bf16_contract_variant"]["objective_rel_diff_vs_fp32"] == 0.0
+    assert abs(out["bf16_variant"]["objective_rel_diff_vs_fp32"] - 5e-7) < 1e-15
+    assert np.array_equal(labels, before)       # the FP32 labels are back
