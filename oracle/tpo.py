@@ -8,7 +8,8 @@ Each function follows one step of the method in the paper's order and
 notation; numpy / scipy primitives (dense and sparse matrix products, QR,
 SVD) serve as single steps, with no blocking, fusion or reordering beyond
 what the paper writes. Where the paper is silent or inconsistent the reading
-taken is named in the docstring (R1..R13, the same list as the design notes).
+taken is named in the docstring of the function that uses it (R1..R13, each
+stated in full below; R14 and R17 with ``nci`` and ``polar``).
 
 Readings used here
   R1  restart form of the propagation: Z_0 = (1-a) X and

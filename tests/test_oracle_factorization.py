@@ -114,3 +114,30 @@ def test_onmf_clamps_and_zero_columns():
     assert np.all(Phi2 >= 0) and np.all(H2 >= 0)
     assert np.all(np.isfinite(Phi2)) and np.all(np.isfinite(H2))
     assert np.all(Phi2[:, 1] == 0) and np.all(H2[:, 1] == 0)
+
+
+def test_seed_factors_signs_and_clamps():
+    # Eq. 18 with reading R8 on a matrix whose SVD is known exactly: Phi = max(Gamma, 0) and
+    # H = max(Psi Sigma, 0), where each left vector carries the sign that makes its entries sum
+    # to >= 0 and its right vector flips with it. Columns are built with mixed signs and with
+    # negative sums, so an unclamped factor, H without Sigma, Sigma on Phi, a sign flip left on
+    # one side only, or H = Psi alone all fail below.
+    rng = np.random.default_rng(31)
+    n, m, r, k = 400, 24, 8, 5
+    U = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    V = np.linalg.qr(rng.standard_normal((m, r)))[0]
+    U[:, 1] *= -np.sign(U[:, 1].sum())          # a column whose entries sum below zero
+    s = np.array([7.0, 4.0, 2.5, 1.6, 1.1, 0.5, 0.3, 0.2])
+    A = (U * s) @ V.T
+    Phi, H, Sig = tpo.seed_factors(A, k, seed=3, oversample=3, power_iters=2)
+    sgn = np.where(U[:, :k].sum(axis=0) < 0, -1.0, 1.0)
+    Gam = U[:, :k] * sgn
+    Psi = V[:, :k] * sgn
+    assert np.allclose(Sig, s[:k], rtol=1e-12)
+    assert np.allclose(Phi, np.maximum(Gam, 0.0), atol=1e-10)
+    assert np.allclose(H, np.maximum(Psi * s[:k], 0.0), atol=1e-10)
+    # both factors really were clamped: the signed vectors have negative entries
+    assert (Gam < -1e-3).any() and (Psi < -1e-3).any()
+    assert Phi.min() == 0.0 and H.min() == 0.0
+    # the flipped column: Gamma's sum >= 0 after the flip, and H follows the same sign
+    assert sgn[1] < 0 and Phi[:, 1].sum() > 0
