@@ -333,12 +333,16 @@ ABG_API int abg_objective(const float* r, int64_t n, int32_t m, int64_t ldr,
  * allocator, a latency-bound loop that cannot absorb an allocation's device
  * synchronisation, a host runtime that forbids libraries to allocate). It calls
  * no cudaMalloc/cudaFree or allocating routine: its scratch is one fixed 24 MiB
- * __device__ array that every GPU loading the library holds until exit. Limit:
- * k * (m + 1) <= 48,393 (else ABG_EINVAL with the limit in abg_last_error()).
- * The first call on a device looks the array up (cudaGetSymbolAddress); make
- * that first call before any stream capture. All calls share the array: calls
- * that overlap on the GPU race. Labels outside [0, k) are skipped. Synchronises
- * `stream`; obj (host) gets {objective, trace_obj}. */
+ * __device__ array per GPU, held until exit. With CUDA's lazy module loading
+ * (the default) that array is reserved by the first call on a device, which
+ * also looks it up (cudaGetSymbolAddress): make that first call before the
+ * application hands all device memory to its own allocator, and before any
+ * stream capture. Limit: k * (m + 1) <= 48,393 (else ABG_EINVAL with the limit
+ * in abg_last_error()). All calls share the array and calls that overlapped on
+ * the GPU would race on it; each call therefore holds a process-wide lock until
+ * `stream` has synchronised, so calls from several host threads run one after
+ * another. Labels outside [0, k) are skipped. obj (host) gets
+ * {objective, trace_obj}. */
 ABG_API int abg_objective_noalloc(const float* r, int64_t n, int32_t m, int64_t ldr,
                                   const int32_t* labels, int32_t k, double* obj, void* stream);
 

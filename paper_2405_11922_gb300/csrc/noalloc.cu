@@ -18,12 +18,15 @@ constexpr int kNoAllocChunks = 128;                 // fixed number of row chunk
 
 // Scratch of every abg_objective_noalloc call on this device. Calls share it
 // and it keeps the last call's contents; the kernels below write every element
-// they later read, so nothing needs clearing. Calls that overlap on the GPU
-// (different streams, or a second call before the first finished on another
-// stream) race on it.
+// they later read, so nothing needs clearing. Calls that overlapped on the GPU
+// would race on it, so each call holds a process-wide lock until its stream has
+// synchronised: calls from several host threads run one after another. With
+// CUDA's lazy module loading the array is reserved when the first call on a
+// device loads this file's kernels, not when the library is loaded.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_mu;
+std::mutex g_mu;       // guards g_addr
+std::mutex g_call_mu;  // serialises whole calls (see abg_objective_noalloc)
 void* g_addr[64] = {};
 
 // Device address of the array for the current device, looked up once per
@@ -166,7 +169,12 @@ extern "C" ABG_API int abg_objective_noalloc(const float* r, int64_t n, int32_t 
   ABG_CHECK(bytes_needed(width) <= (int64_t)kNoAllocBytes, "internal: scratch layout overflow");
   const int64_t rows_per = ceil_div(n, kNoAllocChunks);
   const size_t smem = sizeof(float) * ((size_t)k * 256 + k);
-  ABG_CUDA(cudaFuncSetAttribute(k_na_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // One call at a time in this process, from its first launch until its stream has
+  // synchronised: the launches of two host threads would otherwise interleave in the
+  // array (even on one stream) and one call would read the other's partial sums.
+  std::lock_guard<std::mutex> one_call(g_call_mu);
+  // the limit is only ever raised, so a small-k call never undercuts a larger one
+  ABG_TRY(raise_smem_limit((const void*)k_na_sums, smem));
   for (int col0 = 0; col0 < m; col0 += 256) {
     k_na_sums<<<kNoAllocChunks, 256, smem, s>>>(n, k, m, r, ldr, labels, rows_per, col0, part);
     note_launch();
