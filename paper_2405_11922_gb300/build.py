@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libabg.so")
-SOURCES = ["graph.cu", "batch.cu", "spmm.cu", "dense.cu", "linalg.cu", "pipeline.cu", "server.cu", "noalloc.cu", "tcgemm.cu"]
+SOURCES = ["graph.cu", "batch.cu", "spmm.cu", "dense.cu", "linalg.cu", "pipeline.cu", "server.cu",
+           "noalloc.cu", "tcgemm.cu", "polar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

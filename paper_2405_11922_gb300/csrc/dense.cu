@@ -10,6 +10,7 @@
 //     (Algorithm 3, Eqs. 21-23) and the objective (Eq. 8).
 // All are FP32 SIMT kernels (FMA pipes) tiled through shared memory.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -811,8 +812,9 @@ __global__ void k_nci_finalize(const int* __restrict__ segk, int kmax, const dou
 // 1e-5 s_1): W = M V S_r^+, then T = W V^T. evals = s^2 (descending), evecs = V (columns).
 __global__ void k_polar_w(const int* __restrict__ segk, int kmax, const double* __restrict__ M,
                           const double* __restrict__ evals, const double* __restrict__ evecs,
-                          double* __restrict__ W) {
+                          double* __restrict__ W, const int* __restrict__ skip) {
   const int sg = blockIdx.y;
+  if (skip[sg]) return;  // T already written by the Newton-Schulz iteration
   const int k = segk[sg];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kmax * kmax) return;
@@ -830,8 +832,9 @@ __global__ void k_polar_w(const int* __restrict__ segk, int kmax, const double* 
 
 __global__ void k_polar_t(const int* __restrict__ segk, int kmax, const double* __restrict__ W,
                           const double* __restrict__ evecs, int kp, float* __restrict__ T,
-                          double* __restrict__ t64) {
+                          double* __restrict__ t64, const int* __restrict__ skip) {
   const int sg = blockIdx.y;
+  if (skip[sg]) return;
   const int k = segk[sg];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kmax * kmax) return;
@@ -842,6 +845,15 @@ __global__ void k_polar_t(const int* __restrict__ segk, int kmax, const double* 
     for (int j = 0; j < k; ++j) v += W[o + (int64_t)m * kmax + j] * evecs[o + (int64_t)l * kmax + j];
   if (t64 && m < k && l < k) t64[o + (int64_t)m * kmax + l] = v;
   T[(int64_t)sg * kmax * kp + m * kp + l] = (float)v;
+}
+
+// V_s = I (k_s x k_s, column-major with column stride k_s, inside a kmax x kmax slab)
+__global__ void k_eye_blocks(const int* __restrict__ segk, int kmax, float* __restrict__ V) {
+  const int sg = blockIdx.y;
+  const int k = segk[sg];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= k * k) return;
+  V[(int64_t)sg * kmax * kmax + q] = (q / k == q % k) ? 1.f : 0.f;
 }
 
 __global__ void k_nci_init(int nseg, const int* __restrict__ segk, int kmax, int kp,
@@ -878,13 +890,24 @@ int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ld
   double* S;
   ABG_TRY(scr.get(&S, (size_t)nseg * ((size_t)kmax * kmax + kmax)));
   double *M = nullptr, *W = nullptr, *evals = nullptr, *evecs = nullptr;
-  float* warm = nullptr;  // right singular vectors of the last pass's Phi^T Y
+  float* warm = nullptr;  // right singular vectors of the last Jacobi pass over Phi^T Y
+  int* ns_done = nullptr;  // per segment: the Newton-Schulz iteration gave this pass's T
+  // ABG_POLAR=jacobi: every pass through the Jacobi SVD (for comparisons of the two forms)
+  const char* pe = std::getenv("ABG_POLAR");
+  const bool jacobi_only = pe && std::strcmp(pe, "jacobi") == 0;
   if (procrustes) {
     ABG_TRY(scr.get(&warm, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&M, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&W, (size_t)nseg * kmax * kmax));
     ABG_TRY(scr.get(&evals, (size_t)nseg * kmax));
     ABG_TRY(scr.get(&evecs, (size_t)nseg * kmax * kmax));
+    ABG_TRY(scr.get(&ns_done, (size_t)nseg));
+    ABG_CUDA(cudaMemsetAsync(ns_done, 0, sizeof(int) * nseg, s));
+    // the Jacobi sweeps start from the rotations of the last pass that ran them, the first
+    // time from the identity (the same as no warm start)
+    k_eye_blocks<<<dim3((unsigned)ceil_div((int64_t)kmax * kmax, 256), (unsigned)nseg), 256, 0,
+                   s>>>(ss.k, kmax, warm);
+    note_launch();
   }
   if (passes) passes->assign(nseg, t_g);
   std::vector<int> done(nseg, 0), host(nseg);
@@ -917,12 +940,15 @@ int nci_run(const RowSpace& rs, const SegSizes& ss, const float* phi, int64_t ld
     k_nci_finalize<<<g, 256, 0, s>>>(ss.k, kmax, S, kp, T, t_out, counters + 2 * nseg, M);
     note_launch();
     if (procrustes) {
-      // consecutive passes move few labels, so Phi^T Y changes little: the Jacobi sweeps start
-      // from the previous pass's rotations
-      ABG_TRY(svd_right(nseg, kmax, ss.k, kmax, M, evals, evecs, s, warm, t > 0));
-      k_polar_w<<<g, 256, 0, s>>>(ss.k, kmax, M, evals, evecs, W);
+      // Newton-Schulz on a thread-block cluster; a segment it leaves (done = 0) goes through
+      // the Jacobi SVD, whose sweeps start from the rotations it found last time (consecutive
+      // passes move few labels, so Phi^T Y changes little)
+      if (!jacobi_only)
+        ABG_TRY(polar_newton_schulz(nseg, ss.k, kmax, M, kp, T, t_out, ns_done, s));
+      ABG_TRY(svd_right(nseg, kmax, ss.k, kmax, M, evals, evecs, s, warm, true, ns_done, true));
+      k_polar_w<<<g, 256, 0, s>>>(ss.k, kmax, M, evals, evecs, W, ns_done);
       note_launch();
-      k_polar_t<<<g, 256, 0, s>>>(ss.k, kmax, W, evecs, kp, T, t_out);
+      k_polar_t<<<g, 256, 0, s>>>(ss.k, kmax, W, evecs, kp, T, t_out, ns_done);
       note_launch();
     }
     ABG_LAUNCH_CHECK();

@@ -219,8 +219,18 @@ int objective(const RowSpace& rs, const SegSizes& ss, const float* R, int m, int
 // stride lmax inside an m*lmax slab): FP32 one-sided Jacobi, results FP64 (l_s x l_s slabs of
 // stride lmax). warm (nseg slabs of lmax*lmax floats, optional): the rotations are stored
 // there on exit, and with warm_valid the sweeps start from the ones stored by the last call.
+// skip (device, per segment, optional): segments with a non-zero entry are left untouched.
+// square: segment s is l_s x l_s inside an lmax x lmax slab of zeros (m == lmax), so the
+// orthogonality threshold follows l_s (the same result alone and in a batch).
 int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
-              double* evecs, cudaStream_t s, float* warm = nullptr, bool warm_valid = false);
+              double* evecs, cudaStream_t s, float* warm = nullptr, bool warm_valid = false,
+              const int* skip = nullptr, bool square = false);
+// Orthogonal Procrustes factor of M_s (k_s x k_s in a kmax x kmax FP64 slab) by the
+// Newton-Schulz iteration on a thread-block cluster: T_s (FP32, row stride kp) and t64_s (FP64
+// k x k slab, may be null) are written and done[s] = 1 when the iteration meets the stopping
+// rule that reproduces the 1e-5 s_1 threshold; done[s] = 0 leaves the segment to svd_right.
+int polar_newton_schulz(int nseg, const int* segk, int kmax, const double* M, int kp, float* T,
+                        double* t64, int* done, cudaStream_t s);
 // Gaussian matrix (rows x cols, row stride ld) of each segment from (seeds[s], stream id); the
 // segment's block sits at out + s*oseg; columns >= cols_s (segcols) are set to 0.
 int gaussian_f64(int nseg, const uint64_t* seeds, int stream_id, int rows, int cols, double* out,

@@ -415,11 +415,14 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
                                                        float* __restrict__ Vg_all, int in_smem,
                                                        int max_sweeps, double* __restrict__ evals,
                                                        double* __restrict__ evecs,
-                                                       float* __restrict__ warm, int warm_in) {
+                                                       float* __restrict__ warm, int warm_in,
+                                                       const int* __restrict__ skip,
+                                                       int square) {
   extern __shared__ float sv_smem[];
   __shared__ int s_rot;
   __shared__ unsigned s_maxr;  // largest |cos| between a pair's columns this sweep (float bits)
   const int sg = blockIdx.x;
+  if (skip && skip[sg]) return;  // this segment's factor was found another way
   const int l = segl[sg];
   const double* Bt = Btall + (int64_t)sg * m * lmax;
   // column-major: column j of W at W + j*m, of V at V + j*l
@@ -461,7 +464,10 @@ __global__ void __launch_bounds__(1024) k_svd_onesided(int m, const int* __restr
   // a pair counts as orthogonal below 4 sqrt(m) FP32 ulps of its norms (the rounding level of
   // an m-term FP32 dot product; a fixed 1e-6 sits at that level for m ~ 100 and can keep the
   // sweeps going to max_sweeps), and never above 1e-6 is required
-  const float tol = fmaxf(1e-6f, 4.f * sqrtf((float)m) * 5.9604645e-8f);
+  // (square: the segment's matrix is l x l inside an m x m slab whose other entries are 0,
+  // so its columns are l long; the threshold then depends on the segment alone, and a
+  // segment gives the same result alone and in a batch)
+  const float tol = fmaxf(1e-6f, 4.f * sqrtf((float)(square ? l : m)) * 5.9604645e-8f);
   // G lanes per column pair, so that one pass of the CTA's groups covers a step's P pairs
   // where it can (G >= 8 keeps the column loops a few elements deep per lane)
   const int G = P <= nw ? 32 : (P <= 2 * nw ? 16 : 8);
@@ -587,7 +593,8 @@ __global__ void k_pad_square(const int* __restrict__ segl, int lmax, const doubl
 }
 
 int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, double* evals,
-              double* evecs, cudaStream_t s, float* warm, bool warm_valid) {
+              double* evecs, cudaStream_t s, float* warm, bool warm_valid, const int* skip,
+              bool square) {
   ABG_CHECK(lmax <= kMaxRsvdBlock, "svd: block width above %d", kMaxRsvdBlock);
   Scratch scr(s);
   const size_t smem = sizeof(float) * ((size_t)m * lmax + (size_t)lmax * lmax);
@@ -615,7 +622,8 @@ int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, doub
     k_pad_square<<<g2, 256, 0, s>>>(segl, lmax, R, Rt);
     note_launch();
     ABG_LAUNCH_CHECK();
-    return svd_right(nseg, lmax, segl, lmax, Rt, evals, evecs, s, warm, warm_valid);
+    return svd_right(nseg, lmax, segl, lmax, Rt, evals, evecs, s, warm, warm_valid, skip,
+                     false);
   }
   float *W = nullptr, *V = nullptr;
   if (!in_smem) {
@@ -626,7 +634,8 @@ int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, doub
   }
   if (!in_smem) warm = nullptr;  // the warm start keeps V in shared memory
   k_svd_onesided<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(
-      m, segl, lmax, Bt, W, V, in_smem, 40, evals, evecs, warm, warm && warm_valid ? 1 : 0);
+      m, segl, lmax, Bt, W, V, in_smem, 40, evals, evecs, warm, warm && warm_valid ? 1 : 0, skip,
+      square ? 1 : 0);
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;

@@ -402,3 +402,56 @@ def test_solve_with_nci_variants(planted):
         assert np.array_equal(lab[sure], r["labels"][sure])
         assert res.objective == pytest.approx(r["objective"], rel=1e-5)
         assert res.nci_passes == len(r["changes"])
+
+
+@pytest.mark.parametrize("k", [1, 3, 17, 100, 128])
+def test_procrustes_factor_newton_schulz_and_jacobi(k, monkeypatch):
+    # the two ways to the Procrustes factor (Newton-Schulz on a thread-block cluster, Jacobi
+    # SVD) against the oracle's SVD-based factor, with an empty cluster (a zero column of
+    # Phi^T Y) for k > 3
+    rng = np.random.default_rng(700 + k)
+    n = 4001
+    lab = rng.integers(0, k, n)
+    Phi = np.abs(0.3 * rng.standard_normal((n, k)) / np.sqrt(n))
+    Phi[np.arange(n), lab] += 1.0 / np.sqrt(n / k)
+    if k > 3:
+        Phi[:, 2] = 0.0
+    Phi = Phi.astype(np.float32).astype(np.float64)
+    rl, rT, rm, _ = tpo.nci(Phi, 12, procrustes=True)
+    out = {}
+    for mode in ("newton-schulz", "jacobi"):
+        if mode == "jacobi":
+            monkeypatch.setenv("ABG_POLAR", "jacobi")
+        labels = torch.zeros(n, dtype=torch.int32, device=DEV)
+        T = torch.zeros((k, k), dtype=torch.float64, device=DEV)
+        abg.abg_nci(dev(Phi), n, k, 12, labels, None, T, nci_flags=abg.ABG_NCI_PROCRUSTES)
+        out[mode] = (labels.cpu().numpy(), T.cpu().numpy())
+    monkeypatch.delenv("ABG_POLAR", raising=False)
+    sure = rm > 1e-4
+    for mode, (lb, Tg) in out.items():
+        assert np.array_equal(lb[sure], rl[sure]), mode
+        assert np.abs(Tg - rT).max() < 2e-5 * max(1.0, np.abs(rT).max()), mode
+        keep = np.abs(rT).sum(axis=0) > 1e-8
+        assert np.allclose((Tg.T @ Tg)[np.ix_(keep, keep)], np.eye(keep.sum()), atol=1e-5), mode
+        if k > 3:
+            assert np.all(Tg[:, 2] == 0.0), mode     # the empty cluster's column stays zero
+
+
+def test_procrustes_solve_same_alone_and_in_batch():
+    # segments of different k in one batch: the Procrustes factor (either path) and hence the
+    # labels of each graph are those of its solve alone
+    graphs = [synth.make_small(900 + i, n_u=n, n_v=int(1.4 * n), k=kk, d_u=24, deg=6, signal=2.0)
+              for i, (n, kk) in enumerate([(3000, 40), (1200, 7), (5000, 48), (800, 3)])]
+    params = [abg.params(k=g.k, alpha=0.6, gamma=4, d=24, t_f=4, t_g=12, seed=40 + i,
+                         procrustes=True) for i, g in enumerate(graphs)]
+    batch = abg.abg_batch_create(graphs)
+    labels, results = abg.abg_batch_cluster(batch, params)
+    batch.close()
+    row = 0
+    for g, p, r in zip(graphs, params, results):
+        h = abg.abg_create(g)
+        lab1, r1 = abg.abg_cluster(h, p)
+        h.close()
+        assert np.array_equal(labels[row:row + g.n_u], lab1)
+        assert r.objective == r1.objective
+        row += g.n_u
