@@ -47,7 +47,14 @@ def workload_of(g, scale: float) -> dict:
 
 
 PARAMS = dict(k=100, alpha=0.9, gamma=10, d=128, t_f=5, t_g=20, seed=0)
-ORACLE_SCALES = (0.01, 0.02)   # oracle sample sizes (fraction of the full workload)
+L2_NOTE = "inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"
+
+
+def config_of(nci: str, precision: str, parallelism: str, g=None, scale: float = 1.0) -> dict:
+    """The line's config: the workload (named by its sizes), the T update of Algorithm 3, the
+    arithmetic and where it runs."""
+    return dict(workload_of(g, scale), nci=NCI_NAMES[nci], precision=precision,
+                parallelism=parallelism, l2=L2_NOTE)
 NCI_NAMES = {"procrustes": "Algorithm 3 with T = orthogonal Procrustes factor of Phi^T Y "
                            "(T T^T = I of Eq. 20)",
              "printed": "Algorithm 3 with T = Phi^T Y"}
@@ -194,17 +201,23 @@ def job_value(world: int, steps: int, elapsed_max_s: float) -> float:
 VARIANTS = (("bf16_contract_variant", "bf16-contract (SpMM FP32, products with R in BF16)",
              dict(bf16_contract=True)),
             ("bf16_variant", "bf16 (bf16-contract + bf16-propagation)",
-             dict(bf16_contract=True, bf16_propagation=True)))
+             dict(bf16_contract=True, bf16_propagation=True)),
+            ("printed_t_variant", "fp32, Algorithm 3 as printed (T = Phi^T Y)",
+             dict(procrustes=False)))
 
 
 def time_variants(abg, torch, graph, g, labels, results, stream, args) -> dict:
-    """Time the BF16 variants of the FP32 solve on its resident graph (one untimed solve, then
-    args.steps timed with CUDA events) and compare them with the FP32 result held in
-    `labels` / `results`; `labels` holds the FP32 labels again on return."""
+    """Time the variants of the FP32 solve on its resident graph (the two BF16 options, and
+    Algorithm 3 with the printed T when the steps use the Procrustes T): one untimed solve, then
+    args.steps timed with CUDA events, each compared with the FP32 result held in `labels` /
+    `results`; `labels` holds the FP32 labels again on return."""
     ref_labels = labels.copy()
     out = {}
     for key, desc, flags in VARIANTS:
-        pv = abg.params(**PARAMS, procrustes=args.nci == "procrustes", **flags)
+        flags = dict(dict(procrustes=args.nci == "procrustes"), **flags)
+        if key == "printed_t_variant" and not flags["procrustes"] and args.nci == "printed":
+            continue                      # the timed steps already are this variant
+        pv = abg.params(**PARAMS, **flags)
         abg.abg_cluster(graph, pv, labels, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -273,45 +286,95 @@ def quality_of(g, labels, res) -> dict:
             "objective_eq8": res.objective}
 
 
-def oracle_sample(seed: int = 0, procrustes: bool = True) -> dict:
-    """Time the FP64 oracle on two small instances of the workload generator and extrapolate
-    linearly to the full size (every phase is linear in |U| and |E| at fixed d and k)."""
+ORACLE_SCALE = 0.01   # the oracle's sample: the same generator at 1% of the workload
+
+
+def oracle_graph(seed: int = 0, scale: float = ORACLE_SCALE):
     import synth
+    return synth.make_config3(seed=seed, scale=scale)
+
+
+def oracle_solve_seconds(g, procrustes: bool = True) -> float:
+    """Wall time of one FP64 oracle solve of ``g`` with the workload's parameters."""
     from oracle import tpo
-    times = []
-    for sc in ORACLE_SCALES:
-        g = synth.make_config3(seed=seed, scale=sc)
-        t0 = time.perf_counter()
-        tpo.tpo(g, **PARAMS, procrustes=procrustes)
-        times.append(time.perf_counter() - t0)
-    (s0, s1), (t0, t1) = ORACLE_SCALES, times
-    slope = (t1 - t0) / (s1 - s0)
-    est = max(t1, t1 + slope * (1.0 - s1))
-    return dict(seconds_full_est=est, sample_seconds=times,
-                sample=(f"full oracle solves of the same generator at {s0:g} and {s1:g} of the "
-                        f"workload (|U|={int(2e6 * s0)} and {int(2e6 * s1)}, k=100), "
-                        f"extrapolated linearly in size to |U|=2M"),
-                cores=os.cpu_count())
+    t0 = time.perf_counter()
+    tpo.tpo(g, **PARAMS, procrustes=procrustes)
+    return time.perf_counter() - t0
+
+
+def oracle_threads() -> int:
+    """Threads the oracle's BLAS may use: the thread variables when set, else every core."""
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def oracle_single_thread_seconds(procrustes: bool = True, scale: float = ORACLE_SCALE) -> float:
+    """One oracle solve of the sample in a child process limited to one thread (BLAS thread
+    counts are fixed when numpy loads, so a fresh interpreter is needed)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "g = bench.oracle_graph(scale=%r); print(bench.oracle_solve_seconds(g, %r))"
+            % (ROOT, scale, procrustes))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def sample_note(g, scale: float, what: str) -> str:
+    return (f"{what}: full FP64 oracle solves of the same generator at {scale:g} of the workload "
+            f"(|U|={g.n_u}, |V|={g.n_v}, {g.nnz} edges, k=100, d=128), each timed on the host "
+            f"cores; value = {scale:g} / seconds per sample solve, i.e. the full workload's "
+            "solves/s if the oracle's time grows linearly in |U| and |E| (every step is linear "
+            "in both at fixed d and k)")
+
+
+def cpu_baseline(procrustes: bool) -> dict:
+    """The oracle as it stands on the host cores: one solve of the 1% sample on every thread
+    (after one untimed solve), and one in a single-threaded child process."""
+    g = oracle_graph()
+    oracle_solve_seconds(g, procrustes)
+    t_all = oracle_solve_seconds(g, procrustes)
+    t_one = oracle_single_thread_seconds(procrustes)
+    return {"value": ORACLE_SCALE / t_all, "unit": "solves/s", "cores": oracle_threads(),
+            "kind": "oracle", "sample": sample_note(g, ORACLE_SCALE, "measured"),
+            "measured_sample_s": t_all,
+            "single_thread": {"value": ORACLE_SCALE / t_one, "cores": 1,
+                              "measured_sample_s": t_one}}
 
 
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    vals = []
+    g = oracle_graph()
+    proc = args.nci == "procrustes"
+    secs = []
+    t_start = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
+        t = oracle_solve_seconds(g, proc)
         if i >= args.warmup:
-            vals.append(1.0 / r["seconds_full_est"])
-    v = statistics.median(vals)
+            secs.append(t)
+    timed_s = sum(secs)
+    step_s = statistics.median(secs)
+    v = ORACLE_SCALE / step_s
+    cores = oracle_threads()
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, nci=NCI_NAMES[args.nci], parallelism="cpu oracle"),
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+            "ms_per_step": 1e3 * timed_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args.nci, "fp64 (oracle)",
+                                f"CPU oracle on {cores} host threads"),
+            "step": f"one oracle solve of the workload's generator at {ORACLE_SCALE:g} of its "
+                    f"size (|U|={g.n_u}); ms_per_step is that solve's measured time",
+            "sample_scale": ORACLE_SCALE,
+            "extrapolated_full_s": step_s / ORACLE_SCALE,
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample_note(g, ORACLE_SCALE, "measured"),
+                             "measured_sample_s": step_s},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
 
 
@@ -398,11 +461,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f32+bf16",
         "data": "synthetic",
-        "config": dict(workload_of(g, args.scale), nnz=int(g.nnz),
-                       parallelism=f"{world} independent solves "
-                       "(one graph per rank)" if world > 1 else "single GPU",
-                       precision=args.precision, nci=NCI_NAMES[args.nci],
-                       l2="inputs larger than L2 (graph 1.3 GB, solve working set ~11 GB)"),
+        "config": config_of(args.nci, args.precision,
+                            f"{world} independent solves (one graph per rank)" if world > 1
+                            else "single GPU", g, args.scale),
+        "graph": {"n_u": int(g.n_u), "n_v": int(g.n_v), "nnz": int(g.nnz)},
         "tpo_prop_iters_per_s": PARAMS["gamma"] / (prop_ms / 1e3),
         "spmm_hbm_gbs": achieved,
         "phase_ms": dict(zip(["attributes", "propagation", "features", "svd_nmf", "nci",
@@ -415,10 +477,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
     line.update(variants)
+    if world == 1 and not args.no_systems:
+        # the two systems patterns on their own workloads, against the plain one-graph-at-a-time
+        # FP32 path on the same inputs (same T update of Algorithm 3 as the steps above)
+        proc = args.nci == "procrustes"
+        line["batched"] = batched_measure(abg, torch, args.sys_graphs, 2, 1, proc)
+        line["served"] = served_measure(abg, torch, args.sys_requests, 200.0, 0, args.workers,
+                                        args.max_batch, args.budget_gb, proc)
     if world == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(seed=0, procrustes=args.nci == "procrustes")
-        line["cpu_baseline"] = {"value": 1.0 / r["seconds_full_est"], "unit": "solves/s",
-                                "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+        line["cpu_baseline"] = cpu_baseline(args.nci == "procrustes")
     print(json.dumps(line), flush=True)
 
 
@@ -443,22 +510,26 @@ def _pool_map(fn, items, workers=None):
         return pool.map(fn, items, chunksize=max(1, len(items) // 64))
 
 
-def _params4(abg, g, i):
-    return abg.params(k=g.k, alpha=0.6, gamma=6, d=32, t_f=5, t_g=20, seed=i)
+def _params4(abg, g, i, procrustes=False):
+    return abg.params(k=g.k, alpha=0.6, gamma=6, d=32, t_f=5, t_g=20, seed=i,
+                      procrustes=procrustes)
 
 
-def run_batched(args):
-    import torch
+BATCH_WORKLOAD = ("planted ABGs, |U| log-uniform [500, 50000], |V| = 1.5|U|, 10 edge draws per "
+                  "u, k ~ U{3..30}, binary attributes d_u=300 at 3% reduced to d=32, alpha=0.6, "
+                  "gamma=6, T_f=5, T_g=20")
 
-    import paper_2405_11922_gb300 as abg
-    n = args.graphs
+
+def batched_measure(abg, torch, n: int, steps: int, warmup: int, procrustes: bool) -> dict:
+    """n workload-4 graphs solved one at a time (graphs resident) and as one batch; both with
+    the same parameters, labels compared graph by graph."""
     graphs = _pool_map(_gen_config4, list(range(n)))
-    params = [_params4(abg, g, i) for i, g in enumerate(graphs)]
+    params = [_params4(abg, g, i, procrustes) for i, g in enumerate(graphs)]
     rows = sum(g.n_u for g in graphs)
     stream = torch.cuda.current_stream()
     # ---- plain: one graph at a time, graphs resident ----
     handles = [abg.abg_create(g, stream=stream) for g in graphs]
-    for h, p in list(zip(handles, params))[:args.warmup]:
+    for h, p in list(zip(handles, params))[:max(warmup, 1)]:
         abg.abg_cluster(h, p, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -469,16 +540,16 @@ def run_batched(args):
         h.close()
     # ---- batched: all graphs in one batch, resident ----
     batch = abg.abg_batch_create(graphs, stream=stream)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         abg.abg_batch_cluster(batch, params, stream=stream)
     torch.cuda.synchronize()
     l0 = abg.abg_launch_count()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         blab, bres = abg.abg_batch_cluster(batch, params, stream=stream)
     torch.cuda.synchronize()
-    batch_s = (time.perf_counter() - t0) / args.steps
-    launches = (abg.abg_launch_count() - l0) // args.steps
+    batch_s = (time.perf_counter() - t0) / steps
+    launches = (abg.abg_launch_count() - l0) // steps
     batch.close()
     # ---- end to end: uploads included ----
     t0 = time.perf_counter()
@@ -497,17 +568,29 @@ def run_batched(args):
     for g, lab in zip(graphs, plain_labels):
         same += int(np.array_equal(blab[off:off + g.n_u], lab))
         off += g.n_u
-    line = {"metric": "batched TPO solves/s (many small ABGs per launch) vs one graph at a time",
-            "value": n / batch_s, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * batch_s, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{n} planted ABGs, |U| log-uniform [500, 50000], "
-                                   "|V| = 1.5|U|, 10 edge draws per u, k ~ U{3..30}, binary "
-                                   "attributes d_u=300 at 3% reduced to d=32, alpha=0.6, "
-                                   "gamma=6, T_f=5, T_g=20", "total_u": int(rows)},
+    return {"graphs": n, "total_u": int(rows), "batched_solves_per_s": n / batch_s,
             "plain_solves_per_s": n / plain_s, "speedup_vs_plain": plain_s / batch_s,
+            "ms_per_batch": 1e3 * batch_s,
             "e2e": {"batched_solves_per_s": n / batch_e2e, "plain_solves_per_s": n / plain_e2e},
-            "identical_to_plain": f"{same}/{n}", "gpu_launches_per_batch": int(launches)}
+            "identical_to_plain": f"{same}/{n}", "gpu_launches_per_batch": int(launches),
+            "nci": NCI_NAMES["procrustes" if procrustes else "printed"]}
+
+
+def run_batched(args):
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    r = batched_measure(abg, torch, args.graphs, args.steps, args.warmup,
+                        args.nci == "procrustes")
+    line = {"metric": "batched TPO solves/s (many small ABGs per launch) vs one graph at a time",
+            "value": r["batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.graphs} {BATCH_WORKLOAD}", "total_u": r["total_u"],
+                       "nci": r["nci"]}}
+    line.update({k: r[k] for k in ("plain_solves_per_s", "speedup_vs_plain", "e2e",
+                                   "identical_to_plain", "gpu_launches_per_batch")})
     print(json.dumps(line), flush=True)
 
 
@@ -515,20 +598,28 @@ def run_batched(args):
 # served workload: Poisson arrivals, continuous batching vs plain sequential
 # ---------------------------------------------------------------------------
 
-def run_serve(args):
+SERVE_WORKLOAD = ("Poisson arrivals; graphs as in the mid-size workload with |U| log-uniform "
+                  "[1000, 1e6], |V| = 2.5|U|, 25 draws per u, k ~ U{5..100}, half dense d=128 "
+                  "BF16, half sparse d_u=500 reduced to 64; alpha=0.6, gamma=6, T_f=5, T_g=20")
+
+
+def served_measure(abg, torch, requests: int, rate: float, pool: int, workers: int,
+                   max_batch: int, budget_gb: float, procrustes: bool) -> dict:
+    """`requests` requests arriving as a Poisson process: served by the continuous-batching
+    loop, then the same list one at a time (plain), each timed from its arrival; the served
+    labels are compared with the plain ones. pool = 0 draws a fresh graph per request, else
+    requests cycle through `pool` graphs."""
     import threading
 
-    import torch
-
-    import paper_2405_11922_gb300 as abg
     import synth
-    pool = _pool_map(_gen_config5, list(range(args.pool)))
-    arrivals = synth.config5_arrivals(args.requests, rate=args.rate)
+    n_graphs = requests if pool <= 0 else min(pool, requests)
+    graphs = _pool_map(_gen_config5, list(range(n_graphs)))
+    arrivals = synth.config5_arrivals(requests, rate=rate)
     reqs = []
-    for r in range(args.requests):
-        g = pool[r % len(pool)]
+    for r in range(requests):
+        g = graphs[r % len(graphs)]
         p = abg.params(k=g.params["k"], alpha=0.6, gamma=6, d=g.params["d"], t_f=5, t_g=20,
-                       seed=r)
+                       seed=r, procrustes=procrustes)
         reqs.append((g, p))
     stream = torch.cuda.current_stream()
     # warm-up of both paths on a few requests
@@ -537,8 +628,8 @@ def run_serve(args):
         abg.abg_cluster(h, p, stream=stream)
         h.close()
     # ---- served ----
-    sv = abg.Server(workers=args.workers, max_batch_graphs=args.max_batch,
-                    hbm_budget_bytes=int(args.budget_gb * (1 << 30)))
+    sv = abg.Server(workers=workers, max_batch_graphs=max_batch,
+                    hbm_budget_bytes=int(budget_gb * (1 << 30)))
     rids = [None] * len(reqs)
     t_start = time.perf_counter()
 
@@ -577,22 +668,34 @@ def run_serve(args):
         same += int(np.array_equal(lab, served_labels[i]))
     plain_total = time.perf_counter() - t_start
     q = lambda v, x: float(np.percentile(v, x)) * 1e3
-    line = {"metric": "served TPO solves/s and p50/p99 latency vs plain sequential FP32",
-            "value": len(reqs) / served_total, "unit": "solves/s", "n_gpus": 1,
-            "steps": len(reqs), "warmup": 3, "ms_per_step": 1e3 * served_total / len(reqs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, "
-                                   f"graphs drawn from a pool of {len(pool)}: |U| log-uniform "
-                                   "[1000, 1e6], |V| = 2.5|U|, 25 draws per u, k ~ U{5..100}, "
-                                   "half dense d=128 BF16, half sparse d_u=500 reduced to 64",
-                       "workers": args.workers, "max_batch": args.max_batch},
+    return {"requests": requests, "rate_per_s": rate,
+            "graphs": "a fresh graph per request" if n_graphs == requests
+                      else f"{n_graphs} graphs cycled",
             "served": {"solves_per_s": len(reqs) / served_total, "p50_ms": q(served_lat, 50),
                        "p99_ms": q(served_lat, 99), "batches": stats["batches"],
                        "max_batch": stats["max_batch"]},
             "plain": {"solves_per_s": len(reqs) / plain_total, "p50_ms": q(plain_lat, 50),
                       "p99_ms": q(plain_lat, 99)},
-            "identical_to_plain": f"{same}/{len(reqs)}"}
+            "identical_to_plain": f"{same}/{len(reqs)}", "workers": workers,
+            "max_batch": max_batch, "nci": NCI_NAMES["procrustes" if procrustes else "printed"]}
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2405_11922_gb300 as abg
+    r = served_measure(abg, torch, args.requests, args.rate, args.pool, args.workers,
+                       args.max_batch, args.budget_gb, args.nci == "procrustes")
+    line = {"metric": "served TPO solves/s and p50/p99 latency vs plain sequential FP32",
+            "value": r["served"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 3,
+            "ms_per_step": 1e3 / r["served"]["solves_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.requests} requests at {args.rate}/s, {r['graphs']}; "
+                                   + SERVE_WORKLOAD, "workers": args.workers,
+                       "max_batch": args.max_batch, "nci": r["nci"]},
+            "served": r["served"], "plain": r["plain"],
+            "identical_to_plain": r["identical_to_plain"]}
     print(json.dumps(line), flush=True)
 
 
@@ -655,13 +758,20 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the batched and served measurements added to the default line")
+    ap.add_argument("--sys-graphs", type=int, default=128,
+                    help="default line: graphs of the batched measurement")
+    ap.add_argument("--sys-requests", type=int, default=60,
+                    help="default line: requests of the served measurement (fresh graph each)")
     ap.add_argument("--no-variant", action="store_true",
                     help="skip the BF16 variant timed after the FP32 steps")
     ap.add_argument("--workload", choices=["large", "batched", "serve", "config1", "config2"],
                     default="large")
     ap.add_argument("--graphs", type=int, default=512, help="batched workload: number of graphs")
     ap.add_argument("--requests", type=int, default=200, help="served workload: requests")
-    ap.add_argument("--pool", type=int, default=32, help="served workload: distinct graphs")
+    ap.add_argument("--pool", type=int, default=0,
+                    help="served workload: distinct graphs cycled (0 = a fresh graph per request)")
     ap.add_argument("--rate", type=float, default=200.0, help="served workload: arrivals/s")
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--max-batch", type=int, default=64)

@@ -82,12 +82,19 @@ def test_time_variants_reports_both_bf16_forms_and_restores_labels():
     args = SimpleNamespace(steps=5, nci="procrustes")
     out = bench.time_variants(_FakeAbg(), SimpleNamespace(cuda=_FakeCuda), None, g, labels,
                               [_FakeRes(2.0)], None, args)
-    assert set(out) == {"bf16_contract_variant", "bf16_variant"}
-    for v in out.values():
+    assert set(out) == {"bf16_contract_variant", "bf16_variant", "printed_t_variant"}
+    for key, v in out.items():
         assert v["ms_per_step"] == 10.0 / 5 and v["value"] == 1e3 / 2.0
-        assert v["labels_equal_to_fp32"] == 39 / 40
+        if key != "printed_t_variant":
+            assert v["labels_equal_to_fp32"] == 39 / 40
         assert v["quality"]["clusters_nonempty"] == 4
         assert v["phase_ms"]["propagation"] == 50.0
     assert out["bf16_contract_variant"]["objective_rel_diff_vs_fp32"] == 0.0
     assert abs(out["bf16_variant"]["objective_rel_diff_vs_fp32"] - 5e-7) < 1e-15
+    assert out["printed_t_variant"]["labels_equal_to_fp32"] == 1.0
     assert np.array_equal(labels, before)       # the FP32 labels are back
+    # with the printed T already timed, its variant is not repeated
+    args = SimpleNamespace(steps=5, nci="printed")
+    out = bench.time_variants(_FakeAbg(), SimpleNamespace(cuda=_FakeCuda), None, g, labels,
+                              [_FakeRes(2.0)], None, args)
+    assert set(out) == {"bf16_contract_variant", "bf16_variant"}
