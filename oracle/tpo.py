@@ -24,7 +24,8 @@ Readings used here
   R7  randomized SVD = randomized subspace iteration of Halko, Martinsson and
       Tropp (2011): l = min(k + p, rows, cols) Gaussian columns, q power
       iterations, every block re-orthonormalised; the small factor's SVD gives
-      the top k triplets; each left vector is signed so its entries sum >= 0.
+      the top k triplets; each left vector is signed so that its entry of
+      largest magnitude is positive (the first such entry on ties).
   R8  Phi = max(Gamma, 0), H = max(Psi Sigma, 0) (Eq. 18 with the
       non-negativity Eq. 11 asks for).
   R9  Eqs. 16 / 17 use max(numerator, 0); an entry whose denominator is <= 0
@@ -145,7 +146,8 @@ def randomized_svd(A, k: int, seed: int, stream: int, oversample: int = 10, powe
     Gamma = Qb @ Ub[:, :k]
     Sigma = s[:k].copy()
     Psi = Vt[:k].T.copy()
-    flip = Gamma.sum(axis=0) < 0
+    big = np.argmax(np.abs(Gamma), axis=0)              # first largest |entry| per column
+    flip = Gamma[big, np.arange(Gamma.shape[1])] < 0
     Gamma[:, flip] *= -1.0
     Psi[:, flip] *= -1.0
     return Gamma, Sigma, Psi

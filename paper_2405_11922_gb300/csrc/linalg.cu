@@ -644,13 +644,12 @@ int svd_right(int nseg, int m, const int* segl, int lmax, const double* Bt, doub
 // ---------------------------------------------------------------------------
 // Truncated randomized SVD per segment
 // ---------------------------------------------------------------------------
-// sign_j = +1 if colsum(Q).U[:, j] >= 0 else -1 (left vectors summing >= 0);
-// Bm_s[p][j] = U_s[p][j] sign_j (x sigma_j in mode 1), Uks_s signed (FP64), sigma_s.
+// Bm_s[p][j] = U_s[p][j] (x sigma_j in mode 1), Uks_s (FP64), sigma_s; the sign of each
+// column is fixed later from the left factor (k_colmax_part, k_colsign).
 __global__ void k_rsvd_post(const int* __restrict__ segl, const int* __restrict__ segk, int kfix,
                             int lmax, int kmax, const double* __restrict__ evals,
-                            const double* __restrict__ U, const double* __restrict__ qsum,
-                            int with_sigma, float* __restrict__ Bm, int64_t ldb,
-                            double* __restrict__ Uks, double* __restrict__ sigma_out,
+                            const double* __restrict__ U, int with_sigma, float* __restrict__ Bm,
+                            int64_t ldb, double* __restrict__ Uks, double* __restrict__ sigma_out,
                             int64_t sseg) {
   const int sg = blockIdx.y;
   const int l = segl[sg];
@@ -658,19 +657,109 @@ __global__ void k_rsvd_post(const int* __restrict__ segl, const int* __restrict_
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
   const double* Us = U + (int64_t)sg * lmax * lmax;
-  const double* qs = qsum + (int64_t)sg * lmax;
-  double dot = 0.0;
-  for (int p = 0; p < l; ++p) dot += qs[p] * Us[(int64_t)p * lmax + j];
-  const double sgn = dot < 0.0 ? -1.0 : 1.0;
   const double sigma = sqrt(fmax(evals[(int64_t)sg * lmax + j], 0.0));
   float* Bs = Bm + (int64_t)sg * lmax * ldb;
   double* Uk = Uks + (int64_t)sg * lmax * kmax;
   for (int p = 0; p < l; ++p) {
-    const double u = Us[(int64_t)p * lmax + j] * sgn;
+    const double u = Us[(int64_t)p * lmax + j];
     Uk[(int64_t)p * kmax + j] = u;
     Bs[(int64_t)p * ldb + j] = (float)(with_sigma ? u * sigma : u);
   }
   if (sigma_out) sigma_out[sg * sseg + j] = sigma;
+}
+
+// Sign of each left singular vector (reading R7): its entry of largest magnitude is made
+// positive (the first such row on ties). Pass 1: per 2048-row chunk and column j < k_s, the
+// signed value of the column's largest-magnitude entry over the chunk's rows, in row order.
+__global__ void k_colmax_part(const int* __restrict__ chunk_seg, const int64_t* __restrict__ chunk_row0,
+                              const int* __restrict__ chunk_rows, const int* __restrict__ segk,
+                              int kfix, int kmax, const float* __restrict__ G, int64_t ldg,
+                              float* __restrict__ part) {
+  const int64_t c = blockIdx.x;
+  const int sg = chunk_seg[c];
+  const int k = segk ? segk[sg] : kfix;
+  const int64_t r0 = chunk_row0[c], r1 = r0 + chunk_rows[c];
+  for (int j = threadIdx.x; j < kmax; j += blockDim.x) {
+    float best = 0.f, best_abs = -1.f;
+    if (j < k) {
+      constexpr int U = 8;  // loads in flight together; the comparisons stay in row order
+      int64_t r = r0;
+      for (; r + U <= r1; r += U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = G[(r + u) * ldg + j];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (fabsf(v[u]) > best_abs) {
+            best_abs = fabsf(v[u]);
+            best = v[u];
+          }
+      }
+      for (; r < r1; ++r) {
+        const float v = G[r * ldg + j];
+        if (fabsf(v) > best_abs) {
+          best_abs = fabsf(v);
+          best = v;
+        }
+      }
+    }
+    part[c * kmax + j] = best;
+  }
+}
+
+// Pass 2: per segment and column, the chunk winners in chunk order (the first largest
+// magnitude over the whole column), giving sign_j = -1 when that entry is negative, else +1.
+__global__ void k_colsign(const int* __restrict__ segk, int kfix, int kmax,
+                          const int64_t* __restrict__ seg_group0,
+                          const int64_t* __restrict__ group_chunk0,
+                          const int* __restrict__ group_nchunks, const float* __restrict__ part,
+                          float* __restrict__ sign) {
+  const int sg = blockIdx.x;
+  const int k = segk ? segk[sg] : kfix;
+  const int64_t g0 = seg_group0[sg], g1 = seg_group0[sg + 1];
+  const int64_t c0 = g1 > g0 ? group_chunk0[g0] : 0;
+  const int64_t c1 = g1 > g0 ? group_chunk0[g1 - 1] + group_nchunks[g1 - 1] : 0;
+  for (int j = threadIdx.x; j < kmax; j += blockDim.x) {
+    float best = 0.f, best_abs = -1.f;
+    if (j < k)
+      for (int64_t c = c0; c < c1; ++c) {
+        const float v = part[c * kmax + j];
+        if (fabsf(v) > best_abs) {
+          best_abs = fabsf(v);
+          best = v;
+        }
+      }
+    sign[(int64_t)sg * kmax + j] = best < 0.f ? -1.f : 1.f;
+  }
+}
+
+// G[i][j] <- sign_s[j] G[i][j] (then max(., 0) with relu) for j < k_s of the row's segment
+__global__ void k_apply_sign(int64_t rows, const int* __restrict__ row_seg,
+                             const int* __restrict__ segk, int kfix, int kmax,
+                             const float* __restrict__ sign, int relu, float* __restrict__ G,
+                             int64_t ldg) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= rows * kmax) return;
+  const int64_t i = q / kmax;
+  const int j = (int)(q % kmax);
+  const int sg = row_seg[i];
+  if (j >= (segk ? segk[sg] : kfix)) return;
+  float v = G[i * ldg + j] * sign[(int64_t)sg * kmax + j];
+  if (relu) v = fmaxf(v, 0.f);
+  G[i * ldg + j] = v;
+}
+
+// Uks_s[p][j] *= sign_s[j]: the right factor follows the left one's sign
+__global__ void k_sign_cols(const int* __restrict__ segl, const int* __restrict__ segk, int kfix,
+                            int lmax, int kmax, const float* __restrict__ sign,
+                            double* __restrict__ Uks) {
+  const int sg = blockIdx.y;
+  const int k = segk ? segk[sg] : kfix;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= segl[sg] * kmax) return;
+  const int j = q % kmax;
+  if (j >= k) return;
+  Uks[(int64_t)sg * lmax * kmax + q] *= (double)sign[(int64_t)sg * kmax + j];
 }
 
 __global__ void k_relu_f64_to_f32(int rows, const int* __restrict__ segk, int kmax,
@@ -750,7 +839,7 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   const int64_t kk = round_up(kmax, 4);
   const int64_t l2 = (int64_t)lmax * lmax;
   float *Om, *Y, *T1, *Yt, *T2, *Bm;
-  double *Bt, *evals, *evecs, *qsum, *Uks, *Hd;
+  double *Bt, *evals, *evecs, *Uks, *Hd;
   ABG_TRY(scr.get(&Om, (size_t)nseg * m * ll));
   ABG_TRY(scr.get(&Y, (size_t)rs.rows * ll));
   ABG_TRY(scr.get(&T1, (size_t)rs.rows * ll));
@@ -759,7 +848,6 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   ABG_TRY(scr.get(&Bt, (size_t)nseg * m * lmax));
   ABG_TRY(scr.get(&evals, (size_t)nseg * lmax));
   ABG_TRY(scr.get(&evecs, (size_t)nseg * l2));
-  ABG_TRY(scr.get(&qsum, (size_t)nseg * lmax));
   ABG_TRY(scr.get(&Uks, (size_t)nseg * lmax * kmax));
   ABG_TRY(scr.get(&Hd, (size_t)nseg * m * kmax));
   ABG_TRY(scr.get(&Bm, (size_t)nseg * lmax * kk));
@@ -795,15 +883,15 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
   // B^T = A^T Q (m x l); its SVD gives sigma and the left singular vectors of B
   ABG_TRY(apply_at(in, ss.l, lmax, Y, ll, Bt, T2, ll, s));
   ABG_TRY(svd_right(nseg, m, ss.l, lmax, Bt, evals, evecs, s));
-  ABG_TRY(column_sums(rs, lmax, Y, ll, qsum, lmax, s));
   {
     dim3 g((unsigned)ceil_div(kmax, 128), (unsigned)nseg);
-    k_rsvd_post<<<g, 128, 0, s>>>(ss.l, segk, kfixed, lmax, kmax, evals, evecs, qsum,
-                                  out.left_mode, Bm, kk, Uks, out.sigma, out.sseg);
+    k_rsvd_post<<<g, 128, 0, s>>>(ss.l, segk, kfixed, lmax, kmax, evals, evecs, out.left_mode,
+                                  Bm, kk, Uks, out.sigma, out.sseg);
     note_launch();
   }
   ABG_LAUNCH_CHECK();
-  // left factor: Q * (U_k signed [* Sigma]) with max(., 0) for Phi
+  // left factor Gamma = Q U_k (x Sigma in mode 1), then each column signed so that its entry
+  // of largest magnitude is positive, with max(., 0) for Phi (Eq. 18, reading R8)
   {
     NN a;
     a.A = Y;
@@ -817,8 +905,30 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
     a.K = lmax;
     a.segN = segk;
     a.segK = ss.l;
-    a.epi = out.left_mode == 0 ? Epi::Relu : Epi::Store;
+    a.epi = Epi::Store;
     ABG_TRY(gemm_nn(rs, a, s));
+  }
+  {
+    float *part, *sign;
+    ABG_TRY(scr.get(&part, (size_t)std::max<int64_t>(1, rs.n_chunks) * kmax));
+    ABG_TRY(scr.get(&sign, (size_t)nseg * kmax));
+    if (rs.n_chunks) {
+      k_colmax_part<<<(unsigned)rs.n_chunks, 128, 0, s>>>(rs.chunk_seg, rs.chunk_row0,
+                                                          rs.chunk_rows, segk, kfixed, kmax,
+                                                          out.left, out.ldl, part);
+      note_launch();
+    }
+    k_colsign<<<(unsigned)nseg, 128, 0, s>>>(segk, kfixed, kmax, rs.seg_group0, rs.group_chunk0,
+                                             rs.group_nchunks, part, sign);
+    note_launch();
+    k_apply_sign<<<(unsigned)ceil_div(rs.rows * kmax, 256), 256, 0, s>>>(
+        rs.rows, rs.row_seg, segk, kfixed, kmax, sign, out.left_mode == 0 ? 1 : 0, out.left,
+        out.ldl);
+    note_launch();
+    dim3 g((unsigned)ceil_div((int64_t)lmax * kmax, 256), (unsigned)nseg);
+    k_sign_cols<<<g, 256, 0, s>>>(ss.l, segk, kfixed, lmax, kmax, sign, Uks);
+    note_launch();
+    ABG_LAUNCH_CHECK();
   }
   if (out.right) {  // H_s = max(B_s^T U_k, 0) = max(Psi Sigma, 0)
     dim3 g((unsigned)ceil_div((int64_t)m * kmax, 128), (unsigned)nseg);

@@ -174,17 +174,18 @@ def test_printed_t_collapses_many_clusters_procrustes_keeps_them():
     proc = tpo.tpo(g, procrustes=True, **p)
     assert np.unique(proc["labels"]).size >= 90
     assert metrics.nmi(g.truth, proc["labels"]) >= 0.4
-    # Algorithm 3 feeds its labels back into T: a relative change of 1e-6 in Phi (the size of
-    # the difference between an FP32 and an FP64 evaluation of the steps before it) moves some
-    # labels even on nodes whose final margin exceeds 1e-4, by way of a near-tie in an earlier
-    # pass; 1e-9 moves none. The GPU parity tests of this workload rest on this property.
+    # Algorithm 3 feeds its labels back into T: a change of Phi of the size of the difference
+    # between an FP32 and an FP64 evaluation of the steps before it (1e-5 to 1e-4 of max |Phi|)
+    # moves some labels even on nodes whose final margin exceeds 1e-4, by way of a near-tie in
+    # an earlier pass, while 1e-9 moves none. The GPU parity tests of this workload rest on this.
     sure = proc["margin"] > 1e-4
     moved = {}
-    for eps in (1e-9, 1e-6):
+    for eps in (1e-9, 1e-4):
         rng = np.random.default_rng(0)
-        Phi2 = proc["Phi"] * (1.0 + eps * rng.standard_normal(proc["Phi"].shape))
+        Phi = proc["Phi"]
+        Phi2 = np.maximum(Phi + eps * np.abs(Phi).max() * rng.standard_normal(Phi.shape), 0.0)
         lab2, _, _, _ = tpo.nci(Phi2, p["t_g"], procrustes=True)
         moved[eps] = int(np.count_nonzero(lab2[sure] != proc["labels"][sure]))
         obj2, _ = tpo.objective(proc["R"], lab2, p["k"])
         assert abs(obj2 / proc["objective"] - 1.0) < 2e-5
-    assert moved[1e-9] == 0 and 0 < moved[1e-6] <= 0.005 * sure.sum()
+    assert moved[1e-9] == 0 and 0 < moved[1e-4] <= 0.005 * sure.sum()
