@@ -130,19 +130,31 @@ typedef struct {
  *                         products, halving the bytes each gather reads. The
  *                         products accumulate in FP32 and Z_hat (the last
  *                         round, Eq. 2) is FP32.
- * reserved must be 0. */
+ * options is 0 or ABG_REUSE_PROPAGATION: the solve may take Z_hat (Algorithm
+ * 1: the propagation of Eq. 6 and the row normalisation of Eq. 2) from an
+ * earlier solve on the same graph that had this option and the same alpha,
+ * gamma, d and ABG_BF16_PROPAGATION bit (and, with d < d_u, the same seed,
+ * oversample and power_iters, which fix X' of Eq. 15), and skip the attribute
+ * reduction and the propagation: Z_hat depends on neither k, the NCI options
+ * nor the other seeds. A solve with the option that finds no such Z_hat keeps
+ * its own on the graph (n_u x round_up(d, 4) floats of device memory, held
+ * until abg_destroy or until a solve with other keys replaces it; it counts in
+ * abg_graph_footprint). Labels and objective are bitwise those of a solve
+ * without the option. Ignored for batches (abg_batch_create). Without the
+ * option nothing is kept or reused. */
 #define ABG_NCI_PROCRUSTES 1
 #define ABG_NCI_EARLY_STOP 2
 #define ABG_PRECISION_FP32 0
 #define ABG_BF16_CONTRACT 1
 #define ABG_BF16_PROPAGATION 2
+#define ABG_REUSE_PROPAGATION 1
 typedef struct {
   int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
   int32_t nci_flags;
   double alpha;
   uint64_t seed;
   int32_t precision;
-  int32_t reserved;
+  int32_t options;
 } abg_params;
 
 /* Per-solve report. objective = Eq. 8 with s(u_i,u_j) := R[i].R[j] (minimised);
@@ -162,7 +174,7 @@ typedef struct {
    * seeding + NMF (Algorithm 2), NCI generation (Algorithm 3), the objective */
   float ms_phase[6];
   int32_t nci_passes;       /* NCI passes run (t_g unless ABG_NCI_EARLY_STOP)   */
-  int32_t reserved;
+  int32_t reused_propagation; /* 1: Z_hat came from an earlier solve (ABG_REUSE_PROPAGATION) */
 } abg_result;
 
 ABG_API const char* abg_strerror(int status);
@@ -233,6 +245,7 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, failed, rejected, batches, max_batch, pending, inflight_bytes;
   int64_t latency_us_last;    /* submit -> completion of the last polled request */
+  int64_t propagations_reused; /* completed requests whose solve reused Z_hat */
 } abg_server_stats;
 
 ABG_API void abg_server_opts_default(abg_server_opts* o);
@@ -266,7 +279,7 @@ ABG_API int abg_server_get_stats(abg_server* sv, abg_server_stats* out);
 
 /* Eq. 15 / Section 3.2.1: x_out[n_u][ldo] = Gamma Sigma, the top-d SVD of the
  * graph's X_U (randomized, stream ABG_STREAM_OMEGA_X, each left vector signed
- * so that its entries sum >= 0). */
+ * so that its entry of largest magnitude is positive, the first one on ties). */
 ABG_API int abg_reduce_attributes(const abg_graph* g, int32_t d, int32_t oversample,
                                   int32_t power_iters, uint64_t seed, float* x_out, int64_t ldo,
                                   void* stream);

@@ -38,14 +38,14 @@ class abg_graph_desc(C.Structure):
 class abg_params(C.Structure):
     _fields_ = [("k", _i32), ("gamma", _i32), ("d", _i32), ("t_f", _i32), ("t_g", _i32),
                 ("oversample", _i32), ("power_iters", _i32), ("nci_flags", _i32),
-                ("alpha", _f64), ("seed", _u64), ("precision", _i32), ("reserved", _i32)]
+                ("alpha", _f64), ("seed", _u64), ("precision", _i32), ("options", _i32)]
 
 
 class abg_result(C.Structure):
     _fields_ = [("objective", _f64), ("trace_obj", _f64), ("min_margin", _f64),
                 ("last_changes", _i32), ("empty_clusters", _i32), ("clamped_rows", _i32),
                 ("chol_breakdowns", _i32), ("ms_phase", C.c_float * 6), ("nci_passes", _i32),
-                ("reserved", _i32)]
+                ("reused_propagation", _i32)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "ms_phase" else getattr(self, f))
@@ -59,7 +59,8 @@ class abg_server_opts(C.Structure):
 
 class abg_server_stats(C.Structure):
     _fields_ = [(f, _i64) for f in ("submitted", "completed", "failed", "rejected", "batches",
-                                    "max_batch", "pending", "inflight_bytes", "latency_us_last")]
+                                    "max_batch", "pending", "inflight_bytes", "latency_us_last",
+                                    "propagations_reused")]
 
 
 class AbgError(RuntimeError):
@@ -164,12 +165,13 @@ ABG_NCI_EARLY_STOP = 2
 ABG_PRECISION_FP32 = 0
 ABG_BF16_CONTRACT = 1
 ABG_BF16_PROPAGATION = 2
+ABG_REUSE_PROPAGATION = 1
 
 
 def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5, t_g: int = 20,
            oversample: int = 10, power_iters: int = 4, seed: int = 0, procrustes: bool = False,
            early_stop: bool = False, bf16_propagation: bool = False,
-           bf16_contract: bool = False) -> abg_params:
+           bf16_contract: bool = False, reuse_propagation: bool = False) -> abg_params:
     p = abg_params()
     lib().abg_params_default(C.byref(p))
     p.k, p.alpha, p.gamma, p.d, p.t_f, p.t_g = k, alpha, gamma, d, t_f, t_g
@@ -177,6 +179,7 @@ def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5,
     p.nci_flags = (ABG_NCI_PROCRUSTES if procrustes else 0) | (ABG_NCI_EARLY_STOP if early_stop else 0)
     p.precision = ((ABG_BF16_PROPAGATION if bf16_propagation else 0) |
                    (ABG_BF16_CONTRACT if bf16_contract else 0))
+    p.options = ABG_REUSE_PROPAGATION if reuse_propagation else 0
     return p
 
 

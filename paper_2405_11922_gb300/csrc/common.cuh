@@ -44,6 +44,18 @@ int cuda_status(cudaError_t e, const char* what);
 // Launch check: reports the launch error (not asynchronous faults).
 #define ABG_LAUNCH_CHECK() ABG_CUDA(cudaGetLastError())
 
+// Test hook of the bounded waits, read from ABG_TEST_WAIT_EXPIRY at the start of each solve
+// (abg_cluster, abg_batch_cluster) and held for its duration on the calling thread: with the
+// value "spmm" the first wait of every warp of the TMA-gather SpMM for its first gather group
+// gets no time at all, so it runs out on a copy still in flight and the error path runs
+// (the warp drains its copies under the normal limit). Off (0) by default.
+int test_wait_expiry();
+struct SolveHooks {
+  int prev;
+  SolveHooks();
+  ~SolveHooks();
+};
+
 // kernel launches issued by this library in this process (diagnostic counter)
 void note_launch();
 void note_tc_launch();  // a tensor-core kernel launch (also counted by note_launch)

@@ -514,16 +514,25 @@ int column_sums(const RowSpace& rs, int N, const float* A, int64_t lda, double* 
 // Random features (Eqs. 13-14)
 // ---------------------------------------------------------------------------
 // R[i] <- R'[i] / sqrt(max(R'[i].r_s, 1e-300)) with s the row's segment; one warp per row,
-// the row held in registers (PER values per lane, all loads in flight together).
+// the row held in registers (PER values per lane, all loads in flight together). rf is r in
+// FP32 (read through L1); each lane sums its PER products in FP32 and the lanes' partials are
+// added exactly in (hi, lo) FP32 pairs (Knuth's TwoSum), so the dot keeps the accuracy of a
+// double sum without the GPU's slow FP64 pipe; one lane takes the square root in FP64.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
 template <int PER>
 __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t ldr,
-                               const double* __restrict__ r, const int* __restrict__ row_seg,
+                               const float* __restrict__ rf, const int* __restrict__ row_seg,
                                int* __restrict__ clamped, __nv_bfloat16* __restrict__ R16,
                                int64_t ldr16) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double* rsg = r + (int64_t)row_seg[row] * w2;
+  const float* rsg = rf + (int64_t)row_seg[row] * w2;
   float* rp = R + row * ldr;
   float x[PER];
 #pragma unroll
@@ -531,18 +540,29 @@ __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t
     const int c = lane + 32 * i;
     x[i] = c < w2 ? rp[c] : 0.f;
   }
-  float part = 0.f;
+  float hi = 0.f, lo = 0.f;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int c = lane + 32 * i;
-    if (c < w2) part = fmaf(x[i], (float)rsg[c], part);
+    if (c < w2) hi = fmaf(x[i], __ldg(rsg + c), hi);
   }
-  double dot = (double)part;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-  const bool clamp = !(dot > 1e-300);
-  if (clamp) dot = 1e-300;
-  const float inv = (float)(1.0 / sqrt(dot));
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ho = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float e;
+    two_sum(hi, ho, hi, e);
+    lo += lo2 + e;
+  }
+  float inv = 0.f;
+  int clamp = 0;
+  if (lane == 0) {
+    double dot = (double)hi + (double)lo;
+    clamp = !(dot > 1e-300);
+    if (clamp) dot = 1e-300;
+    inv = (float)(1.0 / sqrt(dot));
+  }
+  inv = __shfl_sync(0xffffffffu, inv, 0);
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int c = lane + 32 * i;
@@ -551,7 +571,12 @@ __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t
     rp[c] = v;
     if (R16) R16[row * ldr16 + c] = __float2bfloat16_rn(v);
   }
-  if (clamp && lane == 0) atomicAdd(clamped + row_seg[row], 1);
+  if (clamp) atomicAdd(clamped + row_seg[row], 1);
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
 }
 
 int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, const float* qt,
@@ -581,10 +606,15 @@ int random_features(const RowSpace& rs, const float* zhat, int d, int64_t ldz, c
                                 2 * d, 2 * d, s));
   const unsigned grid = (unsigned)ceil_div(rs.rows, 8);
   const int w2 = 2 * d;
-#define ABG_RF_CASE(per)                                                                 \
-  if (w2 <= 32 * per) {                                                                  \
-    k_rf_normalise<per><<<grid, 256, 0, s>>>(rs.rows, w2, R, ldr, r, rs.row_seg, clamped_dev, \
-                                             R16, ldr16);                                \
+  float* rf;
+  ABG_TRY(scr.get(&rf, (size_t)rs.nseg * w2));
+  k_f64_to_f32<<<(unsigned)ceil_div((int64_t)rs.nseg * w2, 256), 256, 0, s>>>(
+      (int64_t)rs.nseg * w2, r, rf);
+  note_launch();
+#define ABG_RF_CASE(per)                                                                  \
+  if (w2 <= 32 * per) {                                                                   \
+    k_rf_normalise<per><<<grid, 256, 0, s>>>(rs.rows, w2, R, ldr, rf, rs.row_seg, clamped_dev, \
+                                             R16, ldr16);                                 \
   } else
   ABG_RF_CASE(2) ABG_RF_CASE(4) ABG_RF_CASE(8) ABG_RF_CASE(16) ABG_RF_CASE(32) ABG_RF_CASE(64) {
     set_error("random features: 2d above 2048");

@@ -1,6 +1,8 @@
 // Internal interfaces between the library's translation units.
 #pragma once
 
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "batch.cuh"
@@ -54,6 +56,9 @@ struct abg_graph {
     int64_t* heavy_chunk0 = nullptr; // first chunk of each heavy slot (n_heavy + 1)
   } sched_u, sched_v;
   int* wait_err = nullptr;  // device flag: a bounded wait inside a kernel ran out
+  // Z_hat kept by a solve with ABG_REUSE_PROPAGATION (one at a time; see pipeline.cu)
+  std::mutex zmu;
+  std::shared_ptr<struct ZCache> zcache;
   int64_t footprint = 0;
   void* blocks[64] = {};
   int n_blocks = 0;
@@ -159,8 +164,8 @@ struct NN {
 };
 int gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s);
 // The same product on the tensor cores (tcgen05, three-term tf32 split); *used = false when
-// the shape or layout is outside its limits (N <= 256, 16-byte rows, no sin/cos epilogue)
-// or ABG_TENSOR_CORES=0 is set in the environment.
+// the shape or layout is outside its limits (N <= 256, 16-byte rows; the sin/cos epilogue
+// with one N for all segments) or ABG_TENSOR_CORES=0 is set in the environment.
 int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used);
 // Chunk partials part[c][K][N] (fp32) of a TN product on the tensor cores; *used = false
 // when outside its limits (K, N <= 256, 16-byte rows) or ABG_TENSOR_CORES=0.
@@ -170,8 +175,17 @@ int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, boo
 // the TN case K, N <= 256.
 int tc_gemm_nn16(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used);
 int tc_gemm_tn16(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used);
-// Reads and clears the tensor-core kernels' wait flag (synchronises s).
+// Reads and clears the tensor-core kernels' wait flag (synchronises s): the flag of the solve
+// open on this thread (TcFlagScope), else the process-wide flag the step calls use.
 int tc_wait_flag(cudaStream_t s, int* flag);
+// While alive, the tensor-core kernels launched from this thread report a wait that ran out
+// in `flag` (a device int of the caller's solve, zeroed), so concurrent solves on other
+// threads and streams neither see nor clear each other's reports.
+struct TcFlagScope {
+  int* prev;
+  explicit TcFlagScope(int* flag);
+  ~TcFlagScope();
+};
 // C_s (K_s x N_s, FP64, at C + s*c_seg, row stride ldc) = A^T B over the rows of segment s.
 struct TN {
   const float* A = nullptr;

@@ -7,6 +7,31 @@
 
 #include "internal.cuh"
 
+// Z_hat kept on a graph by a solve with ABG_REUSE_PROPAGATION, and the parameters that fix it
+// (Z_hat depends on alpha, gamma, d, the BF16 storage option and, through X' of Eq. 15 when
+// d < d_u, on the seed, oversample and power_iters; never on k or the NCI options).
+struct ZKey {
+  double alpha = 0.0;
+  int gamma = 0, d = 0, bf16 = 0, oversample = 0, power_iters = 0;
+  uint64_t seed = 0;
+  bool operator==(const ZKey& o) const {
+    return alpha == o.alpha && gamma == o.gamma && d == o.d && bf16 == o.bf16 &&
+           oversample == o.oversample && power_iters == o.power_iters && seed == o.seed;
+  }
+};
+struct ZCache {
+  ZKey key;
+  int device = 0;
+  float* buf = nullptr;
+  int64_t bytes = 0;
+  cudaEvent_t ready = nullptr;  // recorded after the copy into buf
+  ~ZCache() {
+    cudaSetDevice(device);
+    if (ready) cudaEventDestroy(ready);
+    if (buf) cudaFree(buf);  // the last solve that read it has finished (it held a reference)
+  }
+};
+
 using namespace abg;
 
 namespace {
@@ -37,7 +62,7 @@ int abg::check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, i
             "unknown nci_flags %d", p->nci_flags);
   ABG_CHECK((p->precision & ~(ABG_BF16_CONTRACT | ABG_BF16_PROPAGATION)) == 0,
             "unknown precision %d", p->precision);
-  ABG_CHECK(p->reserved == 0, "abg_params.reserved must be 0");
+  ABG_CHECK((p->options & ~ABG_REUSE_PROPAGATION) == 0, "unknown options %d", p->options);
   *d_eff = d;
   return ABG_OK;
 }
@@ -46,6 +71,8 @@ namespace {
 
 // Device outputs of one batched solve.
 struct SolveOut {
+  int reused = 0;                     // Z_hat taken from the graph's ZCache
+  std::shared_ptr<ZCache> zhold;      // keeps that ZCache alive until the solve has finished
   int32_t* labels = nullptr;   // rows
   double* obj = nullptr;       // 2 per segment
   int* counters = nullptr;     // 3 per segment: changes, min margin bits, empty clusters
@@ -214,7 +241,29 @@ int onmf_iterations(const RowSpace& rs, const SegSizes& ss, const float* R, int 
 
 // Algorithms 1-3 and Eq. 8 for every segment of g; ev[0..6] (optional) get the phase
 // boundaries recorded on s.
-int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& ks,
+// Keeps a copy of zhat (count floats) on g for later solves with the same key, replacing the
+// one held before. Best effort: without device memory for the copy nothing is kept.
+int zcache_store(abg_graph* g, const ZKey& key, const float* zhat, int64_t count, cudaStream_t s) {
+  auto c = std::make_shared<ZCache>();
+  c->key = key;
+  c->device = g->device;
+  c->bytes = count * (int64_t)sizeof(float);
+  if (cudaMalloc(&c->buf, (size_t)c->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->buf = nullptr;
+    return ABG_OK;
+  }
+  ABG_CUDA(cudaMemcpyAsync(c->buf, zhat, (size_t)c->bytes, cudaMemcpyDeviceToDevice, s));
+  ABG_CUDA(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
+  ABG_CUDA(cudaEventRecord(c->ready, s));
+  std::lock_guard<std::mutex> lk(g->zmu);
+  if (g->zcache) g->footprint -= g->zcache->bytes;
+  g->zcache = c;
+  g->footprint += c->bytes;
+  return ABG_OK;
+}
+
+int solve_batch(abg_graph* g, const RowSpace& rs, const std::vector<int>& ks,
                 const std::vector<uint64_t>& seeds, const abg_params& p, int d, SolveOut& o,
                 cudaEvent_t* ev, cudaStream_t s) {
   const int nseg = rs.nseg;
@@ -229,18 +278,41 @@ int solve_batch(const abg_graph* g, const RowSpace& rs, const std::vector<int>& 
   ABG_TRY(segsizes_build(&ss, ks, ls, seeds, scr, s));
   if (ev) ABG_CUDA(cudaEventRecord(ev[0], s));
   // ---- Algorithm 1 ----
-  const float* xf;
-  const __nv_bfloat16* xb;
-  int64_t ldx;
-  ABG_TRY(prepare_attributes(g, rs, d, p.oversample, p.power_iters, seeds, scr, s, &xf, &xb, &ldx,
-                             o.breakdowns, (p.precision & ABG_BF16_CONTRACT) != 0));
   const int64_t ldz = round_up(d, 4);
-  float* zhat;
-  ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
-  if (ev) ABG_CUDA(cudaEventRecord(ev[1], s));
-  ABG_TRY(propagate(g, xf, xb, ldx, d, p.alpha, p.gamma, zhat, ldz, s,
-                    (p.precision & ABG_BF16_PROPAGATION) != 0));
-  if (ev) ABG_CUDA(cudaEventRecord(ev[2], s));
+  float* zhat = nullptr;
+  const bool reuse = (p.options & ABG_REUSE_PROPAGATION) && nseg == 1;
+  const bool reduced = d < g->d_u;
+  ZKey key;
+  key.alpha = p.alpha;
+  key.gamma = p.gamma;
+  key.d = d;
+  key.bf16 = (p.precision & ABG_BF16_PROPAGATION) ? 1 : 0;
+  key.oversample = reduced ? p.oversample : 0;
+  key.power_iters = reduced ? p.power_iters : 0;
+  key.seed = reduced ? seeds[0] : 0;
+  if (reuse) {
+    std::lock_guard<std::mutex> lk(g->zmu);
+    if (g->zcache && g->zcache->key == key) o.zhold = g->zcache;
+  }
+  if (o.zhold) {  // Z_hat of an earlier solve with the same key: no reduction, no propagation
+    ABG_CUDA(cudaStreamWaitEvent(s, o.zhold->ready, 0));
+    zhat = o.zhold->buf;
+    o.reused = 1;
+    if (ev) ABG_CUDA(cudaEventRecord(ev[1], s));
+    if (ev) ABG_CUDA(cudaEventRecord(ev[2], s));
+  } else {
+    const float* xf;
+    const __nv_bfloat16* xb;
+    int64_t ldx;
+    ABG_TRY(prepare_attributes(g, rs, d, p.oversample, p.power_iters, seeds, scr, s, &xf, &xb,
+                               &ldx, o.breakdowns, (p.precision & ABG_BF16_CONTRACT) != 0));
+    ABG_TRY(scr.get(&zhat, (size_t)n * ldz));
+    if (ev) ABG_CUDA(cudaEventRecord(ev[1], s));
+    ABG_TRY(propagate(g, xf, xb, ldx, d, p.alpha, p.gamma, zhat, ldz, s,
+                      (p.precision & ABG_BF16_PROPAGATION) != 0));
+    if (ev) ABG_CUDA(cudaEventRecord(ev[2], s));
+    if (reuse) ABG_TRY(zcache_store(g, key, zhat, n * ldz, s));
+  }
   double* q;
   float* qt;
   ABG_TRY(scr.get(&q, (size_t)nseg * d * d));
@@ -296,6 +368,7 @@ int rowspace_of(const abg_graph* g, RowSpace* rs, Scratch& scr, cudaStream_t s) 
 // Run the batched solve of g (one parameter set per segment) and bring results to the host.
 int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int32_t* labels,
                  abg_result* res) {
+  SolveHooks hooks;
   ABG_CHECK(g && ps && labels, "null argument");
   ABG_CHECK(np == g->nseg, "need one parameter set per segment (%d given, %d segments)", np, g->nseg);
   int d = 0;
@@ -323,6 +396,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
   for (int i = 0; i < 7; ++i) ev[i] = e[i].e;
   std::vector<double> obj(2 * nseg);
   std::vector<int> cnt(3 * nseg), cl(nseg), passes;
+  int reused = 0;
   int bd = 0;
   {
     Scratch scr(s);
@@ -336,8 +410,17 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     ABG_TRY(scr.get(&o.breakdowns, 1));
     ABG_CUDA(cudaMemsetAsync(o.clamped, 0, sizeof(int) * nseg, s));
     ABG_CUDA(cudaMemsetAsync(o.breakdowns, 0, sizeof(int), s));
-    ABG_TRY(solve_batch(g, rs, ks, seeds, ps[0], d, o, ev, s));
+    int* tc_flag;  // this solve's own report of a tensor-core wait that ran out
+    ABG_TRY(scr.get(&tc_flag, 1));
+    ABG_CUDA(cudaMemsetAsync(tc_flag, 0, sizeof(int), s));
+    TcFlagScope tc_scope(tc_flag);
+    const int st = solve_batch(g, rs, ks, seeds, ps[0], d, o, ev, s);
+    if (st != ABG_OK) {  // a wait that ran out explains a later failure, and is cleared here
+      const int wst = check_wait_flag(g, s);
+      return wst != ABG_OK ? wst : st;
+    }
     passes = o.passes;
+    reused = o.reused;
     ABG_CUDA(cudaMemcpyAsync(labels, o.labels, sizeof(int32_t) * g->n_u, cudaMemcpyDefault, s));
     ABG_CUDA(cudaMemcpyAsync(obj.data(), o.obj, sizeof(double) * 2 * nseg, cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaMemcpyAsync(cnt.data(), o.counters, sizeof(int) * 3 * nseg, cudaMemcpyDeviceToHost, s));
@@ -364,6 +447,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     r.clamped_rows = cl[i];
     r.chol_breakdowns = bd;
     r.nci_passes = i < (int)passes.size() ? passes[i] : ps[i].t_g;
+    r.reused_propagation = reused;
     for (int j = 0; j < 6; ++j) r.ms_phase[j] = ms[j];
     finite &= std::isfinite(r.objective);
     if (res) res[i] = r;
@@ -397,7 +481,7 @@ ABG_API void abg_params_default(abg_params* p) {
   p->alpha = 0.6;
   p->seed = 0;
   p->precision = ABG_PRECISION_FP32;
-  p->reserved = 0;
+  p->options = 0;
 }
 
 ABG_API int64_t abg_solve_footprint(const abg_graph* g, const abg_params* p) {

@@ -176,6 +176,7 @@ void worker_main(abg_server* sv, int wid) {
         j->status = st;
         j->t_done = now;
         if (st == ABG_OK) sv->stats.completed += 1; else sv->stats.failed += 1;
+        if (st == ABG_OK && res[i].reused_propagation) sv->stats.propagations_reused += 1;
       }
       sv->inflight_bytes -= bytes;
       sv->stats.inflight_bytes = sv->inflight_bytes;

@@ -27,6 +27,7 @@
 // only rounds the fp32 B rows to BF16 (no transpose).
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "batch.cuh"
 #include "internal.cuh"
@@ -71,6 +72,12 @@ struct TcArgs {
   uint32_t b_bytes;
   uint32_t tmem_cols;
   int b_resident;  // BF16 kernel: all K blocks of B stay in shared memory (one segment)
+  int* wait_err;   // device flag of the solve (or the process-wide one): a wait ran out
+  // random features (Eq. 13): C[i][n] = out_scale sin(in_scale acc), C[i][N + n] = ... cos,
+  // and per-tile FP64 column sums of both halves into colsum[tile][2N]
+  int sincos;
+  float in_scale, out_scale;
+  double* colsum;
 };
 
 __device__ __forceinline__ float rna_tf32(float x) {
@@ -187,19 +194,36 @@ __global__ void k_tc_prep_b(const float* __restrict__ B, int64_t ldb, int64_t b_
   }
 }
 
+// 32 consecutive fp32 columns of this thread's TMEM lane, without waiting: the registers are
+// valid only after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct Best {
   float v;
   int i;
   float s;
 };
+// columns arrive in increasing order: a tie keeps the lower index (and sets the margin to 0);
+// selects instead of branches, so the lanes of a warp never diverge
 __device__ __forceinline__ void push_best(Best& b, float v, int i) {
-  if (v > b.v) {  // columns arrive in increasing order: ties keep the lower index
-    b.s = b.v;
-    b.v = v;
-    b.i = i;
-  } else if (v > b.s) {
-    b.s = v;
-  }
+  const bool gt = v > b.v;
+  b.s = gt ? b.v : fmaxf(b.s, v);
+  b.i = gt ? i : b.i;
+  b.v = gt ? v : b.v;
 }
 
 // per-tile epilogue of one accumulator row (this thread's TMEM lane)
@@ -210,15 +234,28 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
   const int64_t gm = row0 + r;
   const bool valid = r < nrows;
   Best b{-INFINITY, 0x7fffffff, -INFINITY};
-  for (int c0 = 0; c0 < p.Np; c0 += 32) {
+  if constexpr (ARGMAX) {
+    // the scores of the row (Np <= 128 columns): all TMEM loads in flight, one wait
+    uint32_t r[4][32];
+    const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16);
+    tmem_ld32_async(ta, r[0]);
+    if (p.Np > 32) tmem_ld32_async(ta + 32, r[1]);
+    if (p.Np > 64) tmem_ld32_async(ta + 64, r[2]);
+    if (p.Np > 96) tmem_ld32_async(ta + 96, r[3]);
+    tmem_wait_ld();
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (32 * c + j < Ns) push_best(b, __uint_as_float(r[c][j]), 32 * c + j);
+    }
+  }
+  for (int c0 = 0; c0 < p.Np && !ARGMAX; c0 += 32) {
     float v[32];
     tmem_ld32(tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
     if (!valid) continue;
-    if constexpr (ARGMAX) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < Ns) push_best(b, v[j], c0 + j);
-    } else {
+    {
       float* crow = p.C + gm * p.ldc;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -275,6 +312,90 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
   }
 }
 
+// Reduce-scatter over the warp: afterwards v[0] of lane l holds the sum over all 32 lanes of
+// their v[l] (31 shuffles; the additions run in a fixed order).
+__device__ __forceinline__ void warp_colsum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < o; ++j) {
+      const float send = up ? v[j] : v[j + o];
+      const float keep = up ? v[j + o] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+// Random-feature epilogue of one tile (Eq. 13): this thread's row of sin / cos values, and the
+// tile's column sums (each warp sums its 32 rows per column in FP32, the four warps' sums are
+// added in FP64 in warp order). cs: shared scratch of 4 x 2 Np floats.
+__device__ void tc_epilogue_sincos(const TcArgs& p, uint32_t tacc, int quad, int lane, int64_t tile,
+                                   int64_t row0, int nrows, float* cs) {
+  const int r = quad * 32 + lane;
+  const int64_t gm = row0 + r;
+  const bool valid = r < nrows;
+  const int N = p.N;
+  float* crow = p.C + gm * p.ldc;
+  for (int c0 = 0; c0 < p.Np; c0 += 32) {
+    float v[32];
+    tmem_ld32(tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+    float sn[32], cn[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      sn[j] = 0.f;
+      cn[j] = 0.f;
+      if (valid && c0 + j < N) {
+        float sv, cv;
+        sincosf(p.in_scale * v[j], &sv, &cv);
+        sn[j] = sv * p.out_scale;
+        cn[j] = cv * p.out_scale;
+      }
+    }
+    if (valid) {
+      // 16-byte stores where four columns are in range; the cos half starts at column N,
+      // so its stores are 16-byte aligned only when N is a multiple of 4
+      const bool cos_vec = (N & 3) == 0;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        const int gn = c0 + j;
+        if (gn + 3 < N) {
+          *reinterpret_cast<float4*>(crow + gn) = make_float4(sn[j], sn[j + 1], sn[j + 2], sn[j + 3]);
+          if (cos_vec) {
+            *reinterpret_cast<float4*>(crow + N + gn) =
+                make_float4(cn[j], cn[j + 1], cn[j + 2], cn[j + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) crow[N + gn + q] = cn[j + q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (gn + q < N) {
+              crow[gn + q] = sn[j + q];
+              crow[N + gn + q] = cn[j + q];
+            }
+        }
+      }
+    }
+    warp_colsum32(sn, lane);
+    warp_colsum32(cn, lane);
+    if (c0 + lane < p.Np) {  // the last 32-column load may reach past Np (a multiple of 16)
+      cs[quad * 2 * p.Np + c0 + lane] = sn[0];
+      cs[quad * 2 * p.Np + p.Np + c0 + lane] = cn[0];
+    }
+  }
+  asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+  for (int c = r; c < 2 * N; c += 128) {
+    const int pos = c < N ? c : p.Np + (c - N);
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sum += (double)cs[q * 2 * p.Np + pos];
+    p.colsum[tile * 2 * N + c] = sum;
+  }
+  asm volatile("bar.sync 1, 128;" ::: "memory");  // cs free for the next tile
+}
+
 // Persistent: CTA c takes tiles c, c + gridDim.x, ...; the stage ring runs across tile
 // boundaries and the accumulator alternates between two TMEM buffers, so the MMAs of a
 // tile overlap the epilogue of the previous one.
@@ -318,7 +439,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = tmem_slot;
   const uint32_t acc_cols = p.tmem_cols / 2;  // columns of one accumulator buffer
   // after a wait has run out anywhere, later CTAs skip their work instead of waiting again
-  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+  bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -440,13 +561,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       const int sg = p.tile_seg[tile];
       const int Ns = p.segN ? p.segN[sg] : p.N;
-      tc_epilogue_row<ARGMAX>(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, sg,
-                              p.tile_row0[tile], p.tile_rows[tile], Ns);
+      bool done_sincos = false;
+      if constexpr (!ARGMAX) {
+        if (p.sincos) {
+          tc_epilogue_sincos(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, tile,
+                             p.tile_row0[tile], p.tile_rows[tile],
+                             reinterpret_cast<float*>(smem + (size_t)S * p.stage_bytes +
+                                                      round_up(8 * (3 * S + 4), 16)));
+          done_sincos = true;
+        }
+      }
+      if (!done_sincos)
+        tc_epilogue_row<ARGMAX>(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, sg,
+                                p.tile_row0[tile], p.tile_rows[tile], Ns);
       tc_fence_before();
       mbar_arrive(tempty0 + 8 * bsel);  // this buffer may take the next accumulator
     }
   }
-  if (bad) atomicExch(&g_tc_wait_err, 1);
+  if (bad) atomicExch(p.wait_err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -484,6 +616,7 @@ struct TnArgs {
   uint32_t op_bytes;                // one operand set (A hi, A lo, B hi, B lo)
   int nops;                         // operand sets (2: split of block b+1 overlaps MMAs of b)
   uint32_t tmem_cols;
+  int* wait_err;                    // as in TcArgs
 };
 
 constexpr int kTnRows = 32;  // rows per block = UMMA K extent of one operand set
@@ -531,7 +664,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+  bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -624,34 +757,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float* rb = reinterpret_cast<const float*>(raw + (size_t)s * p.raw_bytes +
                                                          p.raw_a_bytes);
         const int mvalid = rows - b * kTnRows;  // rows of this block inside the chunk
+        // The source block is 32 rows x ld floats (row-major); operand row rr holds source
+        // column rr over the 32 rows (K-major, 128-byte swizzle). Each unit is a 4 x 4 block:
+        // four float4 row reads, a transpose in registers, four float4 operand writes per part.
+        // A warp covers 32 consecutive columns x 16 rows, so the reads touch four 128-byte row
+        // segments and the writes eight distinct 16-byte bank groups: both take the minimum
+        // four wavefronts (the per-element column reads they replace conflicted 8 ways).
         auto emit = [&](const float* src, int ld, int lim, uint32_t rows_out, unsigned char* hi,
                         unsigned char* lo) {
-          // output unit q: operand row rr (= column of src), 4 consecutive source rows m4*4..+3
-          // (eight lanes fill one 128-byte operand row; a mapping with consecutive lanes on
-          // consecutive rr, free of bank conflicts on the column reads, measured 27% slower)
-          for (uint32_t q = t; q < rows_out * 8; q += 128) {
-            const int rr = (int)(q >> 3), m4 = (int)(q & 7);
-            {
-              const int blk = rr >> 7, rl = rr & 127;
-              float v[4];
+          const uint32_t ncol4 = rows_out / 4;                 // 4-column groups (rows_out % 4 == 0)
+          const uint32_t nunits = ((ncol4 + 7) / 8) * 64;      // 8 column groups x 8 row groups
+          for (uint32_t u = t; u < nunits; u += 128) {
+            const uint32_t g = u >> 5, l = u & 31;
+            const uint32_t c4 = 8 * (g >> 1) + (l & 7);        // column group
+            const int k4 = (int)(4 * (g & 1) + (l >> 3));      // row group (4 source rows)
+            if (c4 >= ncol4) continue;
+            const int c0 = (int)(4 * c4), m0 = 4 * k4;
+            float4 v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int m = m0 + e;
+              v[e] = (c0 < ld && m < mvalid) ? *reinterpret_cast<const float4*>(src + m * ld + c0)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const float cm[4] = {c0 < lim ? 1.f : 0.f, c0 + 1 < lim ? 1.f : 0.f,
+                                 c0 + 2 < lim ? 1.f : 0.f, c0 + 3 < lim ? 1.f : 0.f};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              // column c0 + j over rows m0..m0+3 (columns at or beyond lim are zero)
+              float x[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const int m = m4 * 4 + e;
-                v[e] = (rr < lim && m < mvalid) ? src[m * ld + rr] : 0.f;
+                const float4 r = v[e];
+                const float val = j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
+                x[e] = cm[j] != 0.f ? val : 0.f;
               }
-              float4 h, l;
-              h.x = rna_tf32(v[0]);
-              h.y = rna_tf32(v[1]);
-              h.z = rna_tf32(v[2]);
-              h.w = rna_tf32(v[3]);
-              l.x = rna_tf32(v[0] - h.x);
-              l.y = rna_tf32(v[1] - h.y);
-              l.z = rna_tf32(v[2] - h.z);
-              l.w = rna_tf32(v[3] - h.w);
+              float4 h, lw;
+              h.x = rna_tf32(x[0]);
+              h.y = rna_tf32(x[1]);
+              h.z = rna_tf32(x[2]);
+              h.w = rna_tf32(x[3]);
+              lw.x = rna_tf32(x[0] - h.x);
+              lw.y = rna_tf32(x[1] - h.y);
+              lw.z = rna_tf32(x[2] - h.z);
+              lw.w = rna_tf32(x[3] - h.w);
+              const int rr = c0 + j, blk = rr >> 7, rl = rr & 127;
               const uint32_t off = (uint32_t)blk * kTcM * 128 + (uint32_t)rl * 128 +
-                                   (uint32_t)((m4 ^ (rl & 7)) * 16);
+                                   (uint32_t)((k4 ^ (rl & 7)) * 16);
               *reinterpret_cast<float4*>(hi + off) = h;
-              *reinterpret_cast<float4*>(lo + off) = l;
+              *reinterpret_cast<float4*>(lo + off) = lw;
             }
           }
         };
@@ -697,7 +851,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_arrive(tempty);
     }
   }
-  if (bad) atomicExch(&g_tc_wait_err, 1);
+  if (bad) atomicExch(p.wait_err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -774,7 +928,7 @@ __global__ void __launch_bounds__(kNn16Threads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t acc_cols = p.tmem_cols / 2;
-  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+  bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
 
   if (warp == 0) {
     if (lane == 0 && !bad) {  // producer
@@ -865,7 +1019,7 @@ __global__ void __launch_bounds__(kNn16Threads, 1)
       mbar_arrive(tempty0 + 8 * bsel);
     }
   }
-  if (bad) atomicExch(&g_tc_wait_err, 1);
+  if (bad) atomicExch(p.wait_err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -934,7 +1088,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  bool bad = *reinterpret_cast<volatile int*>(&g_tc_wait_err) != 0;
+  bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
 
   if (warp == 0) {
     if (lane == 0) {  // producer
@@ -1098,7 +1252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_arrive(tempty);
     }
   }
-  if (bad) atomicExch(&g_tc_wait_err, 1);
+  if (bad) atomicExch(p.wait_err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -1116,15 +1270,46 @@ bool tc_disabled() {
 
 }  // namespace
 
+namespace {
+// The flag of the solve running on this thread (TcFlagScope), else the process-wide one.
+thread_local int* t_tc_flag = nullptr;
+std::mutex g_flag_mu;
+int* g_flag_addr[64] = {};
+
+int process_flag(int** out) {
+  int dev = 0;
+  ABG_CUDA(cudaGetDevice(&dev));
+  ABG_CHECK(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  if (!g_flag_addr[dev]) {
+    void* a = nullptr;
+    ABG_CUDA(cudaGetSymbolAddress(&a, g_tc_wait_err));
+    g_flag_addr[dev] = static_cast<int*>(a);
+  }
+  *out = g_flag_addr[dev];
+  return ABG_OK;
+}
+
+int current_flag(int** out) {
+  if (t_tc_flag) {
+    *out = t_tc_flag;
+    return ABG_OK;
+  }
+  return process_flag(out);
+}
+}  // namespace
+
+TcFlagScope::TcFlagScope(int* flag) : prev(t_tc_flag) { t_tc_flag = flag; }
+TcFlagScope::~TcFlagScope() { t_tc_flag = prev; }
+
 int tc_wait_flag(cudaStream_t s, int* flag) {
   *flag = 0;
-  ABG_CUDA(cudaMemcpyFromSymbolAsync(flag, g_tc_wait_err, sizeof(int), 0,
-                                     cudaMemcpyDeviceToHost, s));
+  int* f = nullptr;
+  ABG_TRY(current_flag(&f));
+  ABG_CUDA(cudaMemcpyAsync(flag, f, sizeof(int), cudaMemcpyDeviceToHost, s));
   ABG_CUDA(cudaStreamSynchronize(s));
   if (*flag) {
-    const int zero = 0;
-    ABG_CUDA(cudaMemcpyToSymbolAsync(g_tc_wait_err, &zero, sizeof(int), 0,
-                                     cudaMemcpyHostToDevice, s));
+    ABG_CUDA(cudaMemsetAsync(f, 0, sizeof(int), s));
     ABG_CUDA(cudaStreamSynchronize(s));
   }
   return ABG_OK;
@@ -1134,7 +1319,8 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   static_assert(kTile == kTcM, "row-space tiles must match the UMMA M");
   *used = false;
   if (a.ldc % 4 != 0 || reinterpret_cast<uintptr_t>(a.C) % 16 != 0) return ABG_OK;
-  if (tc_disabled() || a.sincos || a.N > 256 || rs.n_tiles == 0) return ABG_OK;
+  if (tc_disabled() || a.N > 256 || rs.n_tiles == 0) return ABG_OK;
+  if (a.sincos && (a.segN || a.argmax || a.ldc < 2 * a.N)) return ABG_OK;
   if (a.lda % 4 != 0 || reinterpret_cast<uintptr_t>(a.A) % 16 != 0 || rs.rows > INT32_MAX)
     return ABG_OK;
   const auto enc = tensor_map_encoder();
@@ -1180,6 +1366,7 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
       return ABG_OK;
   }
   TcArgs p{};
+  ABG_TRY(current_flag(&p.wait_err));
   p.nkb = nkb;
   p.Np = Np;
   p.N = a.N;
@@ -1203,12 +1390,19 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   p.first = a.first;
   p.changes = a.changes;
   p.minbits = a.minbits;
+  p.sincos = a.sincos ? 1 : 0;
+  p.in_scale = a.in_scale;
+  p.out_scale = a.out_scale;
+  p.colsum = a.colsum_part;
   p.b_bytes = (uint32_t)Np * kTcBK * 4;
   p.stage_bytes = 2 * kTcABytes + 2 * p.b_bytes;  // multiple of 1024
   p.stages = (int)std::max<int64_t>(2, std::min<int64_t>(4, (200 * 1024) / p.stage_bytes));
   p.tmem_cols = 64;  // two accumulator buffers of a power of two >= 32 columns each
   while ((int)p.tmem_cols < 2 * Np) p.tmem_cols *= 2;
-  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 8 * (3 * p.stages + 4);
+  // stages, alignment slack, barriers, and for the sin/cos epilogue its column-sum scratch
+  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 +
+                      round_up(8 * (3 * p.stages + 4), 16) +
+                      (a.sincos ? sizeof(float) * 8 * (size_t)Np : 0);
   if (smem > 227 * 1024) return ABG_OK;
   const void* fn = a.argmax ? (const void*)k_tc_nn<true> : (const void*)k_tc_nn<false>;
   ABG_TRY(raise_smem_limit(fn, smem));
@@ -1233,6 +1427,7 @@ int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, boo
   const auto enc = tensor_map_encoder();
   if (!enc) return ABG_OK;
   TnArgs p{};
+  ABG_TRY(current_flag(&p.wait_err));
   p.K = a.K;
   p.N = a.N;
   p.Np = (int)round_up(a.N, 16);
@@ -1340,6 +1535,7 @@ int tc_gemm_nn16(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
       return ABG_OK;
   }
   TcArgs p{};
+  ABG_TRY(current_flag(&p.wait_err));
   p.nkb = nkb;
   p.Np = Np;
   p.N = a.N;
@@ -1387,6 +1583,7 @@ int tc_gemm_tn16(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, b
   const auto enc = tensor_map_encoder();
   if (!enc) return ABG_OK;
   TnArgs p{};
+  ABG_TRY(current_flag(&p.wait_err));
   p.K = a.K;
   p.N = a.N;
   p.Np = (int)round_up(a.N, 16);

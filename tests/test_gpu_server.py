@@ -176,3 +176,40 @@ def test_served_mixed_precisions_equal_alone():
         lab1, res1 = _alone(g, p)
         assert np.array_equal(lab, lab1) and res.objective == res1.objective
     sv.close()
+
+
+@pytest.mark.parametrize("kind,d_u,d", [("dense_bf16", 24, 24), ("csr_f32", 60, 10)])
+def test_resident_resolves_reuse_the_propagation(kind, d_u, d):
+    # Z_hat depends on alpha, gamma, d (and, with d < d_u, on the reduction's seed): a re-solve
+    # with another k or NCI option takes it from the earlier solve and equals a cold solve
+    g = synth.make_small(640, n_u=5000, n_v=7000, k=5, d_u=d_u, deg=6, x_kind=kind, signal=3.0)
+    h = abg.abg_create(g)
+    base = dict(alpha=0.6, gamma=5, d=d, t_f=4, t_g=10, seed=3)
+    fp0 = h.footprint()
+    lab1, r1 = abg.abg_cluster(h, abg.params(k=5, reuse_propagation=True, **base))
+    assert r1.reused_propagation == 0 and h.footprint() > fp0     # computed, then kept
+    cold1, c1 = abg.abg_cluster(h, abg.params(k=5, **base))
+    assert np.array_equal(lab1, cold1) and r1.objective == c1.objective
+    for k, proc in [(7, False), (4, True)]:
+        p = abg.params(k=k, procrustes=proc, reuse_propagation=True, **base)
+        lab, r = abg.abg_cluster(h, p)
+        assert r.reused_propagation == 1 and r.ms_phase[1] < 0.05
+        cold, c = abg.abg_cluster(h, abg.params(k=k, procrustes=proc, **base))
+        assert c.reused_propagation == 0
+        assert np.array_equal(lab, cold)
+        assert r.objective == c.objective and r.trace_obj == c.trace_obj
+    # another alpha (or, when reduced, another seed) does not match the kept Z_hat
+    other = dict(base, alpha=0.5) if d == d_u else dict(base, seed=4)
+    _, r = abg.abg_cluster(h, abg.params(k=5, reuse_propagation=True, **other))
+    assert r.reused_propagation == 0
+    # through the server: a resident re-solve reuses the Z_hat the last solve left
+    sv = abg.Server(workers=2)
+    p = abg.params(k=6, reuse_propagation=True, **other)
+    rid = sv.submit_resident(h, p)
+    st, lab, res = sv.poll(rid, 60_000_000)
+    assert st == abg.ABG_OK and res.reused_propagation == 1
+    assert sv.stats()["propagations_reused"] == 1
+    cold, c = abg.abg_cluster(h, abg.params(k=6, **other))
+    assert np.array_equal(lab, cold) and res.objective == c.objective
+    sv.close()
+    h.close()

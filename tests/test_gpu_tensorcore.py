@@ -147,3 +147,30 @@ def test_batched_solve_tc_vs_simt():
         assert rt.objective == pytest.approx(ref["objective"], rel=1e-5)
         assert rt.objective == pytest.approx(rs_.objective, rel=1e-5)
         row += g.n_u
+
+
+@pytest.mark.parametrize("n,d", [(5003, 128), (777, 16), (4099, 48), (300, 256), (2000, 12), (1500, 6), (999, 3)])
+def test_random_features_tc_vs_simt_vs_oracle(n, d):
+    # Z_hat Q^T with the sin/cos and column-sum epilogue on the tensor cores (3xTF32) against
+    # the SIMT kernel and the FP64 oracle; ragged last tiles, one zero row (reading R3)
+    rng = np.random.default_rng(40 + d)
+    Zh = tpo.normalize_rows(rng.standard_normal((n, d))).astype(np.float32).astype(np.float64)
+    Zh[3] = 0.0
+    _, _, ref, cl_ref = tpo.random_features(Zh, tpo.orthogonal_matrix(9, d))
+    out = {}
+    for mode in ("tc", "simt"):
+        R = empty(n, 2 * d)
+        t0 = abg.abg_tensor_core_launches()
+        if mode == "simt":
+            with simt():
+                cl = abg.abg_random_features(dev(Zh), n, d, 9, R)
+        else:
+            cl = abg.abg_random_features(dev(Zh), n, d, 9, R)
+        ran_tc = abg.abg_tensor_core_launches() > t0
+        assert ran_tc == (mode == "tc")
+        assert cl == cl_ref
+        out[mode] = host(R, 2 * d)
+    for mode, got in out.items():
+        assert np.abs(got - ref).max() <= 2e-4 * np.abs(ref).max(), mode
+    # the two kernels differ only by the tf32 operand split and the summation order
+    assert np.abs(out["tc"] - out["simt"]).max() <= 5e-5 * np.abs(ref).max()

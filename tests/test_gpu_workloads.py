@@ -12,8 +12,8 @@ with the oracle's.
 Labels. Where no label differs on a node whose final oracle margin exceeds 1e-4 the bar is
 met as stated. Algorithm 3 feeds its labels back into T, so one node that flips at a near-tie
 in some pass (a difference of rounding size between FP32 and FP64) changes T for every later
-pass; the oracle itself moves 10-16 of 20,000 labels at k = 100 under a 1e-6 relative
-perturbation of Phi (pinned on the CPU in test_oracle_rounding.py). The bar then applies to
+pass; the oracle itself moves tens of its 20,000 labels at k = 100 under a perturbation of
+Phi of 1e-4 max|Phi| (pinned on the CPU in test_oracle_rounding.py). The bar then applies to
 the first pass at which the two runs differ: every label that differs there must sit at a
 node whose oracle margin in that pass is at most 1e-4, i.e. the two runs are identical until
 a near-tie splits them. After that they are two valid runs of the iteration, and only their
