@@ -80,10 +80,12 @@ struct TcArgs {
   double* colsum;
 };
 
+// x rounded to tf32 (10 explicit mantissa bits), to nearest with ties away from zero, as an
+// fp32 bit pattern with the low 13 bits zero: half a tf32 ulp (bit 12) is added to the
+// magnitude bits and the rest truncated (a carry moves into the exponent as it should).
+// Integer add and mask run at full rate, unlike the conversion instruction.
 __device__ __forceinline__ float rna_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart
@@ -212,6 +214,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One arrival per warp once all its lanes are done (their shared-memory writes fenced to the
+// async proxy, or their tensor-memory loads fenced): a barrier sized in warps then sees 32x
+// fewer arrivals than one sized in threads, which serialise on the barrier's word.
+__device__ __forceinline__ void warp_arrive(uint32_t bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
 struct Best {
   float v;
   int i;
@@ -234,21 +244,27 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
   const int64_t gm = row0 + r;
   const bool valid = r < nrows;
   Best b{-INFINITY, 0x7fffffff, -INFINITY};
+  int old_label = -1;  // read before the TMEM loads so the two latencies overlap
   if constexpr (ARGMAX) {
-    // the scores of the row (Np <= 128 columns): all TMEM loads in flight, one wait
-    uint32_t r[4][32];
+    if (valid && !p.first) old_label = p.labels[gm];
+    // the scores of the row (Np <= 128 columns), 64 columns per TMEM wait
     const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16);
-    tmem_ld32_async(ta, r[0]);
-    if (p.Np > 32) tmem_ld32_async(ta + 32, r[1]);
-    if (p.Np > 64) tmem_ld32_async(ta + 64, r[2]);
-    if (p.Np > 96) tmem_ld32_async(ta + 96, r[3]);
-    tmem_wait_ld();
-    if (valid) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+    for (int h = 0; h < 2; ++h) {
+      if (64 * h >= p.Np) break;  // uniform over the warp
+      uint32_t r[2][32];
+      tmem_ld32_async(ta + 64 * h, r[0]);
+      if (p.Np > 64 * h + 32) tmem_ld32_async(ta + 64 * h + 32, r[1]);
+      tmem_wait_ld();
+      if (valid) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (32 * c + j < Ns) push_best(b, __uint_as_float(r[c][j]), 32 * c + j);
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = 64 * h + 32 * c + j;
+            if (col < Ns) push_best(b, __uint_as_float(r[c][j]), col);
+          }
+      }
     }
   }
   for (int c0 = 0; c0 < p.Np && !ARGMAX; c0 += 32) {
@@ -296,7 +312,7 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
     float mg = INFINITY;
     if (valid) {
       mg = Ns > 1 ? b.v - b.s : INFINITY;
-      if (!p.first && p.labels[gm] != b.i) changed = 1;
+      if (!p.first && old_label != b.i) changed = 1;
       p.labels[gm] = b.i;
       if (p.margin) p.margin[gm] = mg;
     }
@@ -401,10 +417,17 @@ __device__ void tc_epilogue_sincos(const TcArgs& p, uint32_t tacc, int quad, int
 // tile overlap the epilogue of the previous one.
 //   warp 0: TMA producer      warp 1: TMEM owner + MMA issuer
 //   warps 2-5: tf32 split     warps 6-9: epilogue (TMEM lane quarter = warp % 4)
-template <bool ARGMAX>
-__global__ void __launch_bounds__(kTcThreads, 1)
+// MODE 0: C = acc with the elementwise epilogues; 1: NCI argmax; 2: random features (sin/cos
+// and column sums). SPLITW warps split A; EPIG groups of four epilogue warps take the tiles of
+// alternate accumulator buffers (group g: buffer g), so a slow epilogue keeps up with the MMAs.
+template <int MODE, int SPLITW, int EPIG>
+__global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
     k_tc_nn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bhi_map,
             const __grid_constant__ CUtensorMap blo_map, const TcArgs p, int64_t n_tiles) {
+  constexpr bool ARGMAX = MODE == 1;
+  constexpr int kSplitT = 32 * SPLITW;  // split threads
+  static_assert(EPIG == 1 || EPIG == 2, "one or two epilogue groups");
+  static_assert(MODE != 2 || EPIG == 1, "the sin/cos epilogue's column sums use one group");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -417,12 +440,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(full0 + 8 * i, 1);
-      mbar_init(split0 + 8 * i, 128);
+      mbar_init(split0 + 8 * i, SPLITW);  // one arrival per split warp
       mbar_init(empty0 + 8 * i, 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(tfull0 + 8 * i, 1);
-      mbar_init(tempty0 + 8 * i, 128);
+      mbar_init(tempty0 + 8 * i, 4);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -508,7 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mma_commit(tfull0 + 8 * bsel);  // accumulator complete
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + SPLITW) {
     // split each A block into tf32 hi (in place) and lo parts; zero columns >= K_s
     const int t = threadIdx.x - 64;
     int s = 0;
@@ -517,14 +540,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int sg = p.tile_seg[tile];
       const int Ks = p.segK ? p.segK[sg] : p.K;
       for (int kb = 0; kb < p.nkb; ++kb) {
-        if (!mbar_wait_bounded(full0 + 8 * s, ph)) {
+        const bool ok = mbar_wait_bounded(full0 + 8 * s, ph);
+        if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
           bad = true;
           break;
         }
         float4* a = reinterpret_cast<float4*>(smem + (size_t)s * p.stage_bytes);
         float4* alo = a + kTcABytes / 16;
 #pragma unroll 4
-        for (int q = t; q < (int)(kTcABytes / 16); q += 128) {
+        for (int q = t; q < (int)(kTcABytes / 16); q += kSplitT) {
           const int r = q >> 3;
           const int lc = (q & 7) ^ (r & 7);  // logical 16-byte chunk under the 128-byte swizzle
           const int k0 = kb * kTcBK + lc * 4;
@@ -542,7 +566,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           alo[q] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
-        mbar_arrive(split0 + 8 * s);
+        warp_arrive(split0 + 8 * s);
         if (++s == S) {
           s = 0;
           ph ^= 1u;
@@ -550,10 +574,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // epilogue
+    // epilogue: group g = (warp - 2 - SPLITW) / 4 takes the tiles it == g (mod EPIG)
     const int quad = warp & 3;
-    int it = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    const int grp = (warp - 2 - SPLITW) >> 2;
+    int it = grp;
+    for (int64_t tile = blockIdx.x + (int64_t)grp * gridDim.x; tile < n_tiles;
+         tile += (int64_t)EPIG * gridDim.x, it += EPIG) {
       const int bsel = it & 1;
       bad = bad || !mbar_wait_bounded(tfull0 + 8 * bsel, (it >> 1) & 1);
       bad = __any_sync(0xffffffffu, bad);
@@ -561,21 +587,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       const int sg = p.tile_seg[tile];
       const int Ns = p.segN ? p.segN[sg] : p.N;
-      bool done_sincos = false;
-      if constexpr (!ARGMAX) {
-        if (p.sincos) {
-          tc_epilogue_sincos(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, tile,
-                             p.tile_row0[tile], p.tile_rows[tile],
-                             reinterpret_cast<float*>(smem + (size_t)S * p.stage_bytes +
-                                                      round_up(8 * (3 * S + 4), 16)));
-          done_sincos = true;
-        }
-      }
-      if (!done_sincos)
+      if constexpr (MODE == 2) {
+        tc_epilogue_sincos(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, tile,
+                           p.tile_row0[tile], p.tile_rows[tile],
+                           reinterpret_cast<float*>(smem + (size_t)S * p.stage_bytes +
+                                                    round_up(8 * (3 * S + 4), 16)));
+      } else {
         tc_epilogue_row<ARGMAX>(p, tmem + (uint32_t)bsel * acc_cols, quad, lane, sg,
                                 p.tile_row0[tile], p.tile_rows[tile], Ns);
+      }
       tc_fence_before();
-      mbar_arrive(tempty0 + 8 * bsel);  // this buffer may take the next accumulator
+      warp_arrive(tempty0 + 8 * bsel);  // this buffer may take the next accumulator
     }
   }
   if (bad) atomicExch(p.wait_err, 1);
@@ -643,14 +665,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(rfull0 + 8 * i, 1);
-      mbar_init(rempty0 + 8 * i, 128);
+      mbar_init(rempty0 + 8 * i, 4);  // one arrival per transposing warp
     }
     for (int i = 0; i < NO; ++i) {
-      mbar_init(opfull0 + 8 * i, 128);
+      mbar_init(opfull0 + 8 * i, 4);
       mbar_init(opempty0 + 8 * i, 1);
     }
     mbar_init(tfull, 1);
-    mbar_init(tempty, 128);
+    mbar_init(tempty, 4);  // one arrival per epilogue warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -748,8 +770,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int rows = p.chunk_rows[c];
       const int nb = (rows + kTnRows - 1) / kTnRows;
       for (int b = 0; b < nb; ++b, ++n) {
-        if (!mbar_wait_bounded(rfull0 + 8 * s, ph) ||
-            (n >= NO && !mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u))) {
+        const bool ok = mbar_wait_bounded(rfull0 + 8 * s, ph) &&
+                        (n < NO || mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u));
+        if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
           bad = true;
           break;
         }
@@ -813,8 +836,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         emit(ra, p.ka_box, Ks, a_rows, o, o + a_hi_bytes);
         emit(rb, p.nb_box, Ns, (uint32_t)p.Np, o + 2 * a_hi_bytes, o + 2 * a_hi_bytes + b_hi_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
-        mbar_arrive(rempty0 + 8 * s);
-        mbar_arrive(opfull0 + 8 * os);
+        warp_arrive(rempty0 + 8 * s);
+        warp_arrive(opfull0 + 8 * os);
         if (++os == NO) {
           os = 0;
           op_ph ^= 1u;
@@ -848,13 +871,277 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(tempty);
+      warp_arrive(tempty);
     }
   }
   if (bad) atomicExch(p.wait_err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TN without a raw staging ring: the transposing warps read their 4 x 4 blocks of A and B
+// straight from global memory (16-byte loads, 128-byte row segments per warp), so shared
+// memory holds only the operand sets and two of them fit at K = 256: the split of block
+// b + 1 overlaps the MMAs of block b. Two TMEM accumulators alternate between chunks, so the
+// partial of one chunk drains while the next accumulates.
+//   warp 0: TMEM owner + MMA issuer   warps 1..TW: load, transpose, split
+//   warps TW+1..TW+4: epilogue (chunk partials to global, FP32)
+// ---------------------------------------------------------------------------
+struct Tn2Args {
+  const float* A;
+  int64_t lda;
+  const float* B;
+  int64_t ldb;
+  int K, N, Np, mblk;
+  const int* segK;
+  const int* segN;
+  const int* chunk_seg;
+  const int64_t* chunk_row0;
+  const int* chunk_rows;
+  float* part;     // [chunk][K][N]
+  int nops;
+  uint32_t op_bytes;
+  uint32_t acc_cols;  // TMEM columns of one accumulator (>= mblk * Np)
+  uint32_t tmem_cols;
+  int* wait_err;
+};
+
+template <int TW>
+__global__ void __launch_bounds__(32 * (TW + 5), 1) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_slot;
+  constexpr int kT = 32 * TW;  // transposing threads
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NO = p.nops;
+  unsigned char* ops = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NO * p.op_bytes);
+  const uint32_t opfull0 = smem_addr(bars), opempty0 = opfull0 + 8 * NO,
+                 tfull0 = opempty0 + 8 * NO, tempty0 = tfull0 + 16, drain = tempty0 + 16;
+  const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128, b_hi_bytes = (uint32_t)p.Np * 128;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NO; ++i) {
+      mbar_init(opfull0 + 8 * i, TW);  // one arrival per transposing warp
+      mbar_init(opempty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull0 + 8 * i, 1);
+      mbar_init(tempty0 + 8 * i, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
+
+  if (warp == 0) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = tf32_idesc(p.Np);
+      int os = 0;
+      uint32_t op_ph = 0;
+      int it = 0;
+      bool issued = false;
+      for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x, ++it) {
+        const int abuf = it & 1;
+        if (it >= 2 && !mbar_wait_bounded(tempty0 + 8 * abuf, ((it >> 1) - 1) & 1)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)abuf * p.acc_cols;
+        const int nb = (p.chunk_rows[c] + kTnRows - 1) / kTnRows;
+        for (int b = 0; b < nb; ++b) {
+          if (!mbar_wait_bounded(opfull0 + 8 * os, op_ph)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ob = smem_addr(ops + (size_t)os * p.op_bytes);
+          const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes, b_hi = ob + 2 * a_hi_bytes,
+                         b_lo = b_hi + b_hi_bytes;
+          for (int mb = 0; mb < p.mblk; ++mb) {
+            const uint32_t dcol = acc + (uint32_t)(mb * p.Np);
+            const uint32_t ao = (uint32_t)mb * kTcM * 128;
+#pragma unroll
+            for (int j = 0; j < kTnRows / 8; ++j) {
+              const uint32_t off = 32u * j;
+              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_hi + off), idesc,
+                       (b | j) != 0);
+              mma_tf32(dcol, sw128_desc(a_lo + ao + off), sw128_desc(b_hi + off), idesc, 1u);
+              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_lo + off), idesc, 1u);
+            }
+          }
+          issued = true;
+          mma_commit(opempty0 + 8 * os);  // the operand set may be rewritten
+          if (++os == NO) {
+            os = 0;
+            op_ph ^= 1u;
+          }
+        }
+        if (bad) break;
+        mma_commit(tfull0 + 8 * abuf);  // this chunk's partial is complete
+      }
+      // every MMA issued has finished before the CTA may free its tensor memory
+      if (issued) {
+        mma_commit(drain);
+        if (!mbar_wait_bounded(drain, 0)) bad = true;
+      }
+    }
+  } else if (warp <= TW) {
+    const int t = threadIdx.x - 32;
+    const uint32_t a_rows = (uint32_t)p.mblk * kTcM;
+    int os = 0;
+    uint32_t op_ph = 0;
+    int64_t n = 0;
+    // one 4 x 4 block: rows m0..m0+3 of the chunk block, columns c0..c0+3 of src, as four
+    // float4 row loads (zero outside the block's valid rows and beyond the width lim)
+    auto load4 = [&](const float* src, int64_t ld, int lim, int c0, int m0, int mvalid,
+                     float4 (&v)[4]) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + e;
+        v[e] = (c0 < lim && m < mvalid) ? ld_nc_f4(src + (int64_t)m * ld + c0)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto store4 = [&](const float4 (&v)[4], int c0, int k4, int lim, unsigned char* hi,
+                      unsigned char* lo) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4 r = v[e];
+          const float val = j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
+          x[e] = c0 + j < lim ? val : 0.f;
+        }
+        float4 h, lw;
+        h.x = rna_tf32(x[0]);
+        h.y = rna_tf32(x[1]);
+        h.z = rna_tf32(x[2]);
+        h.w = rna_tf32(x[3]);
+        lw.x = rna_tf32(x[0] - h.x);
+        lw.y = rna_tf32(x[1] - h.y);
+        lw.z = rna_tf32(x[2] - h.z);
+        lw.w = rna_tf32(x[3] - h.w);
+        const int rr = c0 + j, blk = rr >> 7, rl = rr & 127;
+        const uint32_t off = (uint32_t)blk * kTcM * 128 + (uint32_t)rl * 128 +
+                             (uint32_t)((k4 ^ (rl & 7)) * 16);
+        *reinterpret_cast<float4*>(hi + off) = h;
+        *reinterpret_cast<float4*>(lo + off) = lw;
+      }
+    };
+    // units: (column group c4, row group k4); a warp covers 8 column groups x 4 row groups
+    const uint32_t na4 = a_rows / 4, nb4 = (uint32_t)p.Np / 4;
+    const uint32_t ua = ((na4 + 7) / 8) * 64, ub = ((nb4 + 7) / 8) * 64;
+    for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+      const int sg = p.chunk_seg[c];
+      const int Ks = p.segK ? p.segK[sg] : p.K;
+      const int Ns = p.segN ? p.segN[sg] : p.N;
+      const int rows = p.chunk_rows[c];
+      const int nb = (rows + kTnRows - 1) / kTnRows;
+      for (int b = 0; b < nb; ++b, ++n) {
+        const int64_t row0 = p.chunk_row0[c] + (int64_t)b * kTnRows;
+        const int mvalid = rows - b * kTnRows;
+        const float* a_src = p.A + row0 * p.lda;
+        const float* b_src = p.B + row0 * p.ldb;
+        // the loads go out before the wait for a free operand set
+        constexpr int kMaxU = 4;  // units per thread (A and B together), checked at launch
+        float4 v[kMaxU][4];
+        int uc0[kMaxU], uk4[kMaxU], uwhich[kMaxU];
+#pragma unroll
+        for (int q = 0; q < kMaxU; ++q) {
+          const uint32_t u = (uint32_t)t + (uint32_t)q * kT;
+          uwhich[q] = -1;
+          if (u < ua + ub) {
+            const bool isA = u < ua;
+            const uint32_t uu = isA ? u : u - ua;
+            const uint32_t g = uu >> 5, l = uu & 31;
+            const uint32_t c4 = 8 * (g >> 1) + (l & 7);
+            const int k4 = (int)(4 * (g & 1) + (l >> 3));
+            if (c4 < (isA ? na4 : nb4)) {
+              uwhich[q] = isA ? 0 : 1;
+              uc0[q] = (int)(4 * c4);
+              uk4[q] = k4;
+              if (isA)
+                load4(a_src, p.lda, Ks, uc0[q], 4 * k4, mvalid, v[q]);
+              else
+                load4(b_src, p.ldb, Ns, uc0[q], 4 * k4, mvalid, v[q]);
+            }
+          }
+        }
+        const bool ok = n < NO || mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u);
+        if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
+          bad = true;
+          break;
+        }
+        unsigned char* o = ops + (size_t)os * p.op_bytes;
+#pragma unroll
+        for (int q = 0; q < kMaxU; ++q) {
+          if (uwhich[q] == 0)
+            store4(v[q], uc0[q], uk4[q], Ks, o, o + a_hi_bytes);
+          else if (uwhich[q] == 1)
+            store4(v[q], uc0[q], uk4[q], Ns, o + 2 * a_hi_bytes,
+                   o + 2 * a_hi_bytes + b_hi_bytes);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+        warp_arrive(opfull0 + 8 * os);
+        if (++os == NO) {
+          os = 0;
+          op_ph ^= 1u;
+        }
+      }
+    }
+  } else {
+    // epilogue: accumulator rows (the K index) -> partial rows, N columns
+    const int quad = warp & 3;
+    int it = 0;
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
+      const int abuf = it & 1;
+      bad = bad || !mbar_wait_bounded(tfull0 + 8 * abuf, (it >> 1) & 1);
+      bad = __any_sync(0xffffffffu, bad);
+      if (bad) break;
+      tc_fence_after();
+      float* pc = p.part + c * (int64_t)p.K * p.N;
+      for (int mb = 0; mb < p.mblk; ++mb) {
+        const int ka = mb * kTcM + quad * 32 + lane;
+        for (int c0 = 0; c0 < p.Np; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) +
+                        (uint32_t)(abuf * p.acc_cols + mb * p.Np + c0), v);
+          if (ka >= p.K) continue;
+          float* prow = pc + (int64_t)ka * p.N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (c0 + j < p.N) prow[c0 + j] = v[j];
+        }
+      }
+      tc_fence_before();
+      warp_arrive(tempty0 + 8 * abuf);
+    }
+  }
+  if (bad) atomicExch(p.wait_err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(p.tmem_cols)
@@ -1404,13 +1691,66 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
                       round_up(8 * (3 * p.stages + 4), 16) +
                       (a.sincos ? sizeof(float) * 8 * (size_t)Np : 0);
   if (smem > 227 * 1024) return ABG_OK;
-  const void* fn = a.argmax ? (const void*)k_tc_nn<true> : (const void*)k_tc_nn<false>;
-  ABG_TRY(raise_smem_limit(fn, smem));
+  // warp layouts: the argmax epilogue is the slow part of the NCI scores (two epilogue
+  // groups); the plain products are bound by the tf32 split (eight split warps); the sin/cos
+  // epilogue's registers leave room for the base layout only
   const unsigned grid = (unsigned)std::min<int64_t>(rs.n_tiles, num_sms());
-  if (a.argmax)
-    k_tc_nn<true><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
-  else
-    k_tc_nn<false><<<grid, kTcThreads, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+  if (a.argmax) {
+    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<1, 4, 2>, smem));
+    k_tc_nn<1, 4, 2><<<grid, 32 * (2 + 4 + 8), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+  } else if (a.sincos) {
+    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<2, 4, 1>, smem));
+    k_tc_nn<2, 4, 1><<<grid, 32 * (2 + 4 + 4), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+  } else {
+    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<0, 8, 1>, smem));
+    k_tc_nn<0, 8, 1><<<grid, 32 * (2 + 8 + 4), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+  }
+  note_launch();
+  note_tc_launch();
+  ABG_LAUNCH_CHECK();
+  *used = true;
+  return ABG_OK;
+}
+
+// k_tc_tn2 for N <= 128 when two operand sets fit; false in *used otherwise
+static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used) {
+  constexpr int TW = 8;
+  *used = false;
+  Tn2Args p{};
+  p.K = a.K;
+  p.N = a.N;
+  p.Np = (int)round_up(a.N, 16);
+  p.mblk = (int)ceil_div(a.K, kTcM);
+  if (p.Np > 128 || p.mblk > 2) return ABG_OK;
+  // units per transposing thread: A (mblk 128 / 4 column groups) and B (Np / 4), x 8 row
+  // groups, in warps of 8 column groups (k_tc_tn2 holds at most four per thread)
+  const int64_t units = ceil_div(p.mblk * kTcM / 4, 8) * 64 + ceil_div(p.Np / 4, 8) * 64;
+  if (units > 4 * 32 * TW) return ABG_OK;
+  ABG_TRY(current_flag(&p.wait_err));
+  p.A = a.A;
+  p.lda = a.lda;
+  p.B = a.B;
+  p.ldb = a.ldb;
+  p.segK = a.segK;
+  p.segN = a.segN;
+  p.chunk_seg = rs.chunk_seg;
+  p.chunk_row0 = rs.chunk_row0;
+  p.chunk_rows = rs.chunk_rows;
+  p.part = part;
+  p.op_bytes = 2u * p.mblk * kTcM * 128 + 2u * p.Np * 128;
+  p.acc_cols = 32;
+  while ((int)p.acc_cols < p.mblk * p.Np) p.acc_cols *= 2;
+  p.tmem_cols = 2 * p.acc_cols;
+  if (p.tmem_cols > 512) return ABG_OK;
+  size_t smem = 0;
+  for (p.nops = 4; p.nops >= 2; --p.nops) {
+    smem = 1024 + (size_t)p.nops * p.op_bytes + 8 * (2 * p.nops + 5);
+    if (smem <= 220 * 1024) break;
+  }
+  if (p.nops < 2) return ABG_OK;
+  ABG_TRY(raise_smem_limit((const void*)k_tc_tn2<TW>, smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(rs.n_chunks, num_sms());
+  k_tc_tn2<TW><<<grid, 32 * (TW + 5), smem, s>>>(p, rs.n_chunks);
   note_launch();
   note_tc_launch();
   ABG_LAUNCH_CHECK();
@@ -1424,6 +1764,8 @@ int tc_gemm_tn(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, boo
   if (a.lda % 4 != 0 || a.ldb % 4 != 0 || reinterpret_cast<uintptr_t>(a.A) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(a.B) % 16 != 0 || rs.rows > INT32_MAX)
     return ABG_OK;
+  ABG_TRY(tc_gemm_tn2(rs, a, part, s, used));
+  if (*used) return ABG_OK;
   const auto enc = tensor_map_encoder();
   if (!enc) return ABG_OK;
   TnArgs p{};

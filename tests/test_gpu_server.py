@@ -41,7 +41,9 @@ def _alone(g, p):
 
 def test_served_results_equal_alone():
     reqs = _requests()
-    sv = abg.Server(workers=3, max_batch_graphs=6)
+    # a free worker waits up to 30 ms for compatible requests, so batches form however fast
+    # the solves run
+    sv = abg.Server(workers=3, max_batch_graphs=6, batch_window_us=30_000)
     rids = []
     for g, p in reqs:                 # arrivals spread over time so batches form as work runs
         rids.append(sv.submit(g, p))
