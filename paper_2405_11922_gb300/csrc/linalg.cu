@@ -104,111 +104,212 @@ int gaussian_f32(int nseg, const uint64_t* seeds, int stream_id, int rows, int c
 }
 
 // ---------------------------------------------------------------------------
-// One CTA per segment: Cholesky G_s = R^T R (R upper, positive diagonal) and
-// R^-1 in FP64 (shared memory when both triangles fit; both are written out). A non-positive (or
-// relatively negligible) pivot zeroes that row of R and that column of R^-1
-// (the column of Q it would produce is dropped) and is counted in *breakdowns.
-// Slabs: G_s at G + s*gseg (row stride ldg); R_s, Ri_s at R + s*l*l with l the
-// segment's size (row stride l); ri32_s (optional) at ri32 + s*r32seg.
+// Blocked Cholesky R^T R = G (upper R, FP64) over many SMs, and R^-1 by columns.
+// Right-looking, 32-column blocks: the diagonal block is factored by one warp per segment
+// (one square root and one division per pivot), the block row to its right is solved with
+// the diagonal block's inverse, and the trailing upper triangle is updated by one thread per
+// element. A pivot at or below 1e-13 max diag(G) counts as a breakdown: its row of R (and its
+// column of R^-1) stays zero, as in the unblocked form. R (and Ri) of segment s use the
+// segment's own l_s as row stride inside their slabs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_inv(const int* __restrict__ segl, int lfix,
-                                                   const double* __restrict__ Gall, int64_t ldg,
-                                                   int64_t gseg, double* __restrict__ Rall,
-                                                   double* __restrict__ Riall, int64_t rseg,
-                                                   float* __restrict__ ri32all, int64_t ldr32,
-                                                   int64_t r32seg, int* __restrict__ breakdowns,
-                                                   int in_smem) {
-  extern __shared__ double csm[];
-  const int sg = blockIdx.x;
+constexpr int kCholB = 32;
+
+// R = upper triangle of G (zeros below); tol_s = 1e-13 max_i G_s[i][i]
+__global__ void k_chol_init(const int* __restrict__ segl, int lfix, const double* __restrict__ Gall,
+                            int64_t ldg, int64_t gseg, double* __restrict__ Rall, int64_t rseg,
+                            double* __restrict__ tol) {
+  const int sg = blockIdx.y;
   const int l = segl ? segl[sg] : lfix;
   const double* G = Gall + sg * gseg;
-  double* Rg = Rall + sg * rseg;
-  double* Rig = Riall + sg * rseg;
-  float* ri32 = ri32all ? ri32all + sg * r32seg : nullptr;
-  double* R = in_smem ? csm : Rg;
-  double* Ri = in_smem ? csm + (int64_t)l * l : Rig;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-  __shared__ double s_piv;
-  __shared__ double s_maxdiag;
-  __shared__ double s_rinv[kMaxRsvdBlock];
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
+  double* R = Rall + sg * rseg;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)l * l;
+       q += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(q / l), j = (int)(q % l);
     R[q] = j >= i ? G[(int64_t)i * ldg + j] : 0.0;
   }
-  if (tid == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
     double m = 0.0;
-    for (int i = 0; i < l; ++i) m = fmax(m, fabs(G[(int64_t)i * ldg + i]));
-    s_maxdiag = m;
-  }
-  __syncthreads();
-  const double tol = 1e-13 * s_maxdiag;
-  // FP64 divisions and square roots are slow: one of each per pivot, multiplications elsewhere
-  double* rinv = s_rinv;
-  for (int j = 0; j < l; ++j) {
-    if (tid == 0) {
-      const double p = R[(int64_t)j * l + j];
-      if (!(p > tol)) {
-        s_piv = 0.0;
-        rinv[j] = 0.0;
-        atomicAdd(breakdowns, 1);
-      } else {
-        s_piv = sqrt(p);
-        rinv[j] = 1.0 / s_piv;
-      }
-    }
-    __syncthreads();
-    const double piv = s_piv, ip = rinv[j];
-    for (int c = j + tid; c < l; c += nt) {
-      const double v = R[(int64_t)j * l + c];
-      R[(int64_t)j * l + c] = piv > 0.0 ? (c == j ? piv : v * ip) : 0.0;
-    }
-    __syncthreads();
-    for (int r = j + 1 + warp; r < l; r += nw) {
-      const double rjr = R[(int64_t)j * l + r];
-      for (int c = r + lane; c < l; c += 32) R[(int64_t)r * l + c] -= rjr * R[(int64_t)j * l + c];
-    }
-    __syncthreads();
-  }
-  // Ri = R^-1 (upper triangular), one row at a time from the bottom:
-  // Ri[i][j] = -(1/R[i][i]) sum_{i<p<=j} R[i][p] Ri[p][j], Ri[i][i] = 1/R[i][i]
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt) Ri[q] = 0.0;
-  __syncthreads();
-  for (int i = l - 1; i >= 0; --i) {
-    const double ii = rinv[i];
-    for (int j = i + tid; j < l; j += nt) {
-      double v;
-      if (j == i) {
-        v = ii;
-      } else {
-        double acc = 0.0;
-        for (int p = i + 1; p <= j; ++p) acc += R[(int64_t)i * l + p] * Ri[(int64_t)p * l + j];
-        v = -ii * acc;
-      }
-      Ri[(int64_t)i * l + j] = v;
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  for (int64_t q = tid; q < (int64_t)l * l; q += nt) {
-    const double v = Ri[q];
-    if (in_smem) {
-      Rig[q] = v;
-      Rg[q] = R[q];
-    }
-    if (ri32) ri32[(q / l) * ldr32 + (q % l)] = (float)v;
+    for (int i = threadIdx.x; i < l; i += 32) m = fmax(m, fabs(G[(int64_t)i * ldg + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) tol[sg] = 1e-13 * m;
   }
 }
 
+// Diagonal block k of each segment (one warp): factor in place, and its upper-triangular
+// inverse into D_s (32 x 32, row stride 32).
+__global__ void k_chol_diag(const int* __restrict__ segl, int lfix, int k, double* __restrict__ Rall,
+                            int64_t rseg, const double* __restrict__ tol, double* __restrict__ Dall,
+                            int* __restrict__ breakdowns) {
+  __shared__ double a[kCholB][kCholB + 1];
+  __shared__ double rinv[kCholB];
+  const int sg = blockIdx.x;
+  const int l = segl ? segl[sg] : lfix;
+  const int o = k * kCholB;
+  if (o >= l) return;
+  const int bs = min(kCholB, l - o);
+  double* R = Rall + sg * rseg;
+  const int c = threadIdx.x;  // this lane's column of the block
+  for (int r = 0; r < bs; ++r) a[r][c] = (c < bs && c >= r) ? R[(int64_t)(o + r) * l + o + c] : 0.0;
+  __syncwarp();
+  const double t = tol[sg];
+  for (int j = 0; j < bs; ++j) {
+    if (c == 0) {
+      const double pv = a[j][j];
+      if (!(pv > t)) {
+        rinv[j] = 0.0;
+        a[j][j] = 0.0;
+        atomicAdd(breakdowns, 1);
+      } else {
+        const double sq = sqrt(pv);
+        a[j][j] = sq;
+        rinv[j] = 1.0 / sq;
+      }
+    }
+    __syncwarp();
+    const double ip = rinv[j];
+    if (c > j && c < bs) a[j][c] = a[j][c] * ip;  // 0 after a breakdown
+    __syncwarp();
+    if (c > j && c < bs) {
+      const double ajc = a[j][c];
+      for (int r = j + 1; r <= c; ++r) a[r][c] -= a[j][r] * ajc;
+    }
+    __syncwarp();
+  }
+  for (int r = 0; r < bs; ++r)
+    if (c < bs && c >= r) R[(int64_t)(o + r) * l + o + c] = a[r][c];
+  // column c of the block's inverse by back substitution (zero column after a breakdown)
+  double x[kCholB];
+#pragma unroll
+  for (int r = 0; r < kCholB; ++r) x[r] = 0.0;
+  if (c < bs) {
+    x[c] = rinv[c];
+    for (int r = c - 1; r >= 0; --r) {
+      double acc = 0.0;
+      for (int q = r + 1; q <= c; ++q) acc += a[r][q] * x[q];
+      x[r] = -rinv[r] * acc;
+    }
+  }
+  double* D = Dall + (int64_t)sg * kCholB * kCholB;
+#pragma unroll
+  for (int r = 0; r < kCholB; ++r) D[r * kCholB + c] = x[r];
+}
+
+// Block row k to the right of the diagonal block: R[o+t][j] = sum_{s <= t} D[s][t] R[o+s][j]
+__global__ void k_chol_panel(const int* __restrict__ segl, int lfix, int k, double* __restrict__ Rall,
+                             int64_t rseg, const double* __restrict__ Dall) {
+  __shared__ double D[kCholB][kCholB];
+  const int sg = blockIdx.y;
+  const int l = segl ? segl[sg] : lfix;
+  const int o = k * kCholB;
+  for (int q = threadIdx.x; q < kCholB * kCholB; q += blockDim.x)
+    D[q / kCholB][q % kCholB] = Dall[(int64_t)sg * kCholB * kCholB + q];
+  __syncthreads();
+  if (o + kCholB >= l) return;
+  const int j = o + kCholB + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= l) return;
+  double* R = Rall + sg * rseg;
+  double v[kCholB];
+#pragma unroll
+  for (int s2 = 0; s2 < kCholB; ++s2) v[s2] = R[(int64_t)(o + s2) * l + j];
+#pragma unroll
+  for (int t = kCholB - 1; t >= 0; --t) {  // top-down would overwrite inputs still needed
+    double acc = 0.0;
+#pragma unroll
+    for (int s2 = 0; s2 <= t; ++s2) acc += D[s2][t] * v[s2];
+    R[(int64_t)(o + t) * l + j] = acc;
+  }
+}
+
+// Trailing update: R[i][j] -= sum_t R[o+t][i] R[o+t][j] for o + 32 <= i <= j < l
+__global__ void k_chol_update(const int* __restrict__ segl, int lfix, int k, int m,
+                              double* __restrict__ Rall, int64_t rseg) {
+  const int sg = blockIdx.y;
+  const int l = segl ? segl[sg] : lfix;
+  const int o = k * kCholB, base = o + kCholB;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)m * m) return;
+  const int i = base + (int)(q / m), j = base + (int)(q % m);
+  if (j < i || j >= l) return;
+  double* R = Rall + sg * rseg;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int t = 0; t < kCholB; ++t) acc += R[(int64_t)(o + t) * l + i] * R[(int64_t)(o + t) * l + j];
+  R[(int64_t)i * l + j] -= acc;
+}
+
+// Ri = R^-1 column by column, one warp per column: x[c] = 1/R[c][c], then for r < c
+// x[r] = -(1/R[r][r]) sum_{r < p <= c} R[r][p] x[p] (lanes split the sum); a zero pivot gives
+// a zero row of R and a zero column of Ri. ri32 (optional) gets an FP32 copy.
+__global__ void k_tri_inv_cols(const int* __restrict__ segl, int lfix, const double* __restrict__ Rall,
+                               int64_t rseg, double* __restrict__ Riall, float* __restrict__ ri32all,
+                               int64_t ldr32, int64_t r32seg) {
+  extern __shared__ double xs[];  // per warp: x (l values)
+  const int sg = blockIdx.y;
+  const int l = segl ? segl[sg] : lfix;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= l) return;  // whole warps
+  const double* R = Rall + sg * rseg;
+  double* Ri = Riall + sg * rseg;
+  float* ri32 = ri32all ? ri32all + sg * r32seg : nullptr;
+  double* x = xs + (int64_t)warp * l;
+  auto inv = [&](int r) {
+    const double d = R[(int64_t)r * l + r];
+    return d > 0.0 ? 1.0 / d : 0.0;
+  };
+  for (int r = lane; r < l; r += 32) x[r] = 0.0;
+  __syncwarp();
+  if (lane == 0) x[c] = inv(c);
+  __syncwarp();
+  for (int r = c - 1; r >= 0; --r) {
+    double acc = 0.0;
+    for (int p2 = r + 1 + lane; p2 <= c; p2 += 32) acc += R[(int64_t)r * l + p2] * x[p2];
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
+    if (lane == 0) x[r] = -inv(r) * acc;
+    __syncwarp();
+  }
+  for (int r = lane; r < l; r += 32) {
+    Ri[(int64_t)r * l + c] = x[r];
+    if (ri32) ri32[(int64_t)r * ldr32 + c] = (float)x[r];
+  }
+}
+
+// Cholesky G_s = R^T R (R upper, positive diagonal) and R^-1 in FP64 per segment. A non-positive
+// (or relatively negligible) pivot zeroes that row of R and that column of R^-1 (the column of
+// Q it would produce is dropped) and is counted in *breakdowns. Slabs: G_s at G + s*gseg (row
+// stride ldg); R_s, Ri_s at R + s*rseg with the segment's own l as row stride; ri32_s
+// (optional) at ri32 + s*r32seg (row stride ldr32).
 static int chol_inv(int nseg, const int* segl, int lmax, const double* G, int64_t ldg, int64_t gseg,
                     double* R, double* Ri, int64_t rseg, float* ri32, int64_t ldr32, int64_t r32seg,
                     int* breakdowns, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 2 * (size_t)lmax * lmax;
-  const int in_smem = smem <= 200 * 1024;
-  if (in_smem) ABG_TRY(raise_smem_limit((const void*)k_chol_inv, smem));
-  k_chol_inv<<<(unsigned)nseg, 1024, in_smem ? smem : 0, s>>>(segl, lmax, G, ldg, gseg, R, Ri, rseg,
-                                                              ri32, ldr32, r32seg, breakdowns,
-                                                              in_smem);
+  Scratch scr(s);
+  double *tol, *D;
+  ABG_TRY(scr.get(&tol, (size_t)nseg));
+  ABG_TRY(scr.get(&D, (size_t)nseg * kCholB * kCholB));
+  const int64_t l2 = (int64_t)lmax * lmax;
+  k_chol_init<<<dim3((unsigned)std::min<int64_t>(ceil_div(l2, 256), 1024), (unsigned)nseg), 256, 0,
+                s>>>(segl, lmax, G, ldg, gseg, R, rseg, tol);
+  note_launch();
+  const int nb = (int)ceil_div(lmax, kCholB);
+  for (int k = 0; k < nb; ++k) {
+    k_chol_diag<<<(unsigned)nseg, 32, 0, s>>>(segl, lmax, k, R, rseg, tol, D, breakdowns);
+    note_launch();
+    const int m = lmax - (k + 1) * kCholB;  // trailing columns of the largest segment
+    if (m <= 0) continue;
+    k_chol_panel<<<dim3((unsigned)ceil_div(m, 128), (unsigned)nseg), 128, 0, s>>>(segl, lmax, k, R,
+                                                                                 rseg, D);
+    note_launch();
+    k_chol_update<<<dim3((unsigned)ceil_div((int64_t)m * m, 256), (unsigned)nseg), 256, 0, s>>>(
+        segl, lmax, k, m, R, rseg);
+    note_launch();
+  }
+  const int wpb = 4;  // columns (warps) per CTA
+  const size_t smem = sizeof(double) * wpb * (size_t)lmax;
+  ABG_TRY(raise_smem_limit((const void*)k_tri_inv_cols, smem));
+  k_tri_inv_cols<<<dim3((unsigned)ceil_div(lmax, wpb), (unsigned)nseg), 32 * wpb, smem, s>>>(
+      segl, lmax, R, rseg, Ri, ri32, ldr32, r32seg);
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;

@@ -894,6 +894,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 //   warp 0: TMEM owner + MMA issuer   warps 1..TW: load, transpose, split
 //   warps TW+1..TW+4: epilogue (chunk partials to global, FP32)
 // ---------------------------------------------------------------------------
+constexpr int kTn2Units = 3;  // 4 x 4 blocks per transposing thread and row block
+
 struct Tn2Args {
   const float* A;
   int64_t lda;
@@ -913,8 +915,9 @@ struct Tn2Args {
   int* wait_err;
 };
 
+// 13 warps put four on one SM sub-partition, whose 16K registers allow 128 a thread
 template <int TW>
-__global__ void __launch_bounds__(32 * (TW + 5), 1) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
+__global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -1049,66 +1052,87 @@ __global__ void __launch_bounds__(32 * (TW + 5), 1) k_tc_tn2(const Tn2Args p, in
         *reinterpret_cast<float4*>(lo + off) = lw;
       }
     };
-    // units: (column group c4, row group k4); a warp covers 8 column groups x 4 row groups
+    // units: (column group c4, row group k4); a warp covers 8 column groups x 4 row groups.
+    // A thread's units are the same for every block; which block they read changes.
     const uint32_t na4 = a_rows / 4, nb4 = (uint32_t)p.Np / 4;
     const uint32_t ua = ((na4 + 7) / 8) * 64, ub = ((nb4 + 7) / 8) * 64;
-    for (int64_t c = blockIdx.x; c < n_chunks && !bad; c += gridDim.x) {
+    constexpr int kMaxU = kTn2Units;  // units per thread (A and B together), checked at launch
+    int uc0[kMaxU], uk4[kMaxU], uwhich[kMaxU];
+#pragma unroll
+    for (int q = 0; q < kMaxU; ++q) {
+      const uint32_t u = (uint32_t)t + (uint32_t)q * kT;
+      uwhich[q] = -1;
+      uc0[q] = 0;
+      uk4[q] = 0;
+      if (u < ua + ub) {
+        const bool isA = u < ua;
+        const uint32_t uu = isA ? u : u - ua;
+        const uint32_t g = uu >> 5, l = uu & 31;
+        const uint32_t c4 = 8 * (g >> 1) + (l & 7);
+        if (c4 < (isA ? na4 : nb4)) {
+          uwhich[q] = isA ? 0 : 1;
+          uc0[q] = (int)(4 * c4);
+          uk4[q] = (int)(4 * (g & 1) + (l >> 3));
+        }
+      }
+    }
+    auto nblocks = [&](int64_t c) { return (p.chunk_rows[c] + kTnRows - 1) / kTnRows; };
+    // the loads of slot q of block b of chunk c into registers (issued, not waited for)
+    auto issue = [&](float4 (&v)[4], int q, int64_t c, int b) {
+      const int sg = p.chunk_seg[c];
+      const int mvalid = p.chunk_rows[c] - b * kTnRows;
+      const int64_t row0 = p.chunk_row0[c] + (int64_t)b * kTnRows;
+      if (uwhich[q] == 0)
+        load4(p.A + row0 * p.lda, p.lda, p.segK ? p.segK[sg] : p.K, uc0[q], 4 * uk4[q], mvalid,
+              v);
+      else if (uwhich[q] == 1)
+        load4(p.B + row0 * p.ldb, p.ldb, p.segN ? p.segN[sg] : p.N, uc0[q], 4 * uk4[q], mvalid,
+              v);
+    };
+    // One register set, rolled: right after slot q of block b is transposed into its operand
+    // set, slot q of the thread's next block is loaded into the same registers, so every load
+    // has one whole block period to arrive.
+    float4 v[kMaxU][4];
+    int64_t c = blockIdx.x;
+    int b = 0;
+    if (c < n_chunks) {
+#pragma unroll
+      for (int q = 0; q < kMaxU; ++q) issue(v[q], q, c, 0);
+    }
+    while (c < n_chunks && !bad) {
+      int64_t c2 = c;
+      int b2 = b;
+      if (++b2 >= nblocks(c2)) {
+        c2 += gridDim.x;
+        b2 = 0;
+      }
+      const bool more = c2 < n_chunks;
+      const bool ok = n < NO || mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u);
+      if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
+        bad = true;
+        break;
+      }
       const int sg = p.chunk_seg[c];
       const int Ks = p.segK ? p.segK[sg] : p.K;
       const int Ns = p.segN ? p.segN[sg] : p.N;
-      const int rows = p.chunk_rows[c];
-      const int nb = (rows + kTnRows - 1) / kTnRows;
-      for (int b = 0; b < nb; ++b, ++n) {
-        const int64_t row0 = p.chunk_row0[c] + (int64_t)b * kTnRows;
-        const int mvalid = rows - b * kTnRows;
-        const float* a_src = p.A + row0 * p.lda;
-        const float* b_src = p.B + row0 * p.ldb;
-        // the loads go out before the wait for a free operand set
-        constexpr int kMaxU = 4;  // units per thread (A and B together), checked at launch
-        float4 v[kMaxU][4];
-        int uc0[kMaxU], uk4[kMaxU], uwhich[kMaxU];
+      unsigned char* o = ops + (size_t)os * p.op_bytes;
 #pragma unroll
-        for (int q = 0; q < kMaxU; ++q) {
-          const uint32_t u = (uint32_t)t + (uint32_t)q * kT;
-          uwhich[q] = -1;
-          if (u < ua + ub) {
-            const bool isA = u < ua;
-            const uint32_t uu = isA ? u : u - ua;
-            const uint32_t g = uu >> 5, l = uu & 31;
-            const uint32_t c4 = 8 * (g >> 1) + (l & 7);
-            const int k4 = (int)(4 * (g & 1) + (l >> 3));
-            if (c4 < (isA ? na4 : nb4)) {
-              uwhich[q] = isA ? 0 : 1;
-              uc0[q] = (int)(4 * c4);
-              uk4[q] = k4;
-              if (isA)
-                load4(a_src, p.lda, Ks, uc0[q], 4 * k4, mvalid, v[q]);
-              else
-                load4(b_src, p.ldb, Ns, uc0[q], 4 * k4, mvalid, v[q]);
-            }
-          }
-        }
-        const bool ok = n < NO || mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u);
-        if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
-          bad = true;
-          break;
-        }
-        unsigned char* o = ops + (size_t)os * p.op_bytes;
-#pragma unroll
-        for (int q = 0; q < kMaxU; ++q) {
-          if (uwhich[q] == 0)
-            store4(v[q], uc0[q], uk4[q], Ks, o, o + a_hi_bytes);
-          else if (uwhich[q] == 1)
-            store4(v[q], uc0[q], uk4[q], Ns, o + 2 * a_hi_bytes,
-                   o + 2 * a_hi_bytes + b_hi_bytes);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
-        warp_arrive(opfull0 + 8 * os);
-        if (++os == NO) {
-          os = 0;
-          op_ph ^= 1u;
-        }
+      for (int q = 0; q < kMaxU; ++q) {
+        if (uwhich[q] == 0)
+          store4(v[q], uc0[q], uk4[q], Ks, o, o + a_hi_bytes);
+        else if (uwhich[q] == 1)
+          store4(v[q], uc0[q], uk4[q], Ns, o + 2 * a_hi_bytes, o + 2 * a_hi_bytes + b_hi_bytes);
+        if (more) issue(v[q], q, c2, b2);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
+      warp_arrive(opfull0 + 8 * os);
+      if (++os == NO) {
+        os = 0;
+        op_ph ^= 1u;
+      }
+      ++n;
+      c = c2;
+      b = b2;
     }
   } else {
     // epilogue: accumulator rows (the K index) -> partial rows, N columns
@@ -1723,9 +1747,9 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.mblk = (int)ceil_div(a.K, kTcM);
   if (p.Np > 128 || p.mblk > 2) return ABG_OK;
   // units per transposing thread: A (mblk 128 / 4 column groups) and B (Np / 4), x 8 row
-  // groups, in warps of 8 column groups (k_tc_tn2 holds at most four per thread)
+  // groups, in warps of 8 column groups (k_tc_tn2 holds at most kTn2Units per thread)
   const int64_t units = ceil_div(p.mblk * kTcM / 4, 8) * 64 + ceil_div(p.Np / 4, 8) * 64;
-  if (units > 4 * 32 * TW) return ABG_OK;
+  if (units > kTn2Units * 32 * TW) return ABG_OK;
   ABG_TRY(current_flag(&p.wait_err));
   p.A = a.A;
   p.lda = a.lda;
