@@ -7,8 +7,8 @@
 //   * CholeskyQR2 of tall FP32 blocks (FP64 Gram / Cholesky, FP32 apply);
 //   * the truncated randomized SVD of Halko, Martinsson and Tropp (subspace
 //     iteration) used by Algorithm 2's seeding (Eq. 18) and by the attribute
-//     reduction of Section 3.2.1 (Eq. 15): the small l x l eigenproblem runs
-//     as a one-CTA parallel cyclic Jacobi in FP64 per segment.
+//     reduction of Section 3.2.1 (Eq. 15): the small SVD of B^T = A^T Q runs as
+//     a one-sided (Hestenes) Jacobi in FP32, one CTA per segment.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -137,12 +137,14 @@ __global__ void k_chol_init(const int* __restrict__ segl, int lfix, const double
 }
 
 // Diagonal block k of each segment (one warp): factor in place, and its upper-triangular
-// inverse into D_s (32 x 32, row stride 32).
-__global__ void k_chol_diag(const int* __restrict__ segl, int lfix, int k, double* __restrict__ Rall,
-                            int64_t rseg, const double* __restrict__ tol, double* __restrict__ Dall,
-                            int* __restrict__ breakdowns) {
-  __shared__ double a[kCholB][kCholB + 1];
-  __shared__ double rinv[kCholB];
+// inverse into D_s (32 x 32, row stride 32). Lane c holds column c of the block in registers;
+// every lane computes each pivot's square root and reciprocal itself (no serial lane), and
+// row j of the factor reaches the other lanes by shuffles.
+__global__ void __launch_bounds__(32) k_chol_diag(const int* __restrict__ segl, int lfix, int k,
+                                                  double* __restrict__ Rall, int64_t rseg,
+                                                  const double* __restrict__ tol,
+                                                  double* __restrict__ Dall,
+                                                  int* __restrict__ breakdowns) {
   const int sg = blockIdx.x;
   const int l = segl ? segl[sg] : lfix;
   const int o = k * kCholB;
@@ -150,49 +152,48 @@ __global__ void k_chol_diag(const int* __restrict__ segl, int lfix, int k, doubl
   const int bs = min(kCholB, l - o);
   double* R = Rall + sg * rseg;
   const int c = threadIdx.x;  // this lane's column of the block
-  for (int r = 0; r < bs; ++r) a[r][c] = (c < bs && c >= r) ? R[(int64_t)(o + r) * l + o + c] : 0.0;
-  __syncwarp();
+  double a[kCholB], rinv[kCholB];
+#pragma unroll
+  for (int r = 0; r < kCholB; ++r)
+    a[r] = (c < bs && r <= c) ? R[(int64_t)(o + r) * l + o + c] : 0.0;
   const double t = tol[sg];
-  for (int j = 0; j < bs; ++j) {
-    if (c == 0) {
-      const double pv = a[j][j];
-      if (!(pv > t)) {
-        rinv[j] = 0.0;
-        a[j][j] = 0.0;
-        atomicAdd(breakdowns, 1);
-      } else {
-        const double sq = sqrt(pv);
-        a[j][j] = sq;
-        rinv[j] = 1.0 / sq;
+#pragma unroll
+  for (int j = 0; j < kCholB; ++j) {
+    rinv[j] = 0.0;
+    if (j < bs) {  // uniform over the warp
+      const double pv = __shfl_sync(0xffffffffu, a[j], j);
+      const bool ok = pv > t;
+      const double sq = ok ? sqrt(pv) : 0.0;
+      const double ip = ok ? 1.0 / sq : 0.0;
+      if (!ok && c == 0) atomicAdd(breakdowns, 1);
+      rinv[j] = ip;
+      a[j] = c == j ? sq : (c > j ? a[j] * ip : a[j]);  // row j (0 after a breakdown)
+#pragma unroll
+      for (int r = j + 1; r < kCholB; ++r) {
+        const double rjr = __shfl_sync(0xffffffffu, a[j], r);  // R[j][r]
+        if (c >= r) a[r] = fma(-rjr, a[j], a[r]);
       }
     }
-    __syncwarp();
-    const double ip = rinv[j];
-    if (c > j && c < bs) a[j][c] = a[j][c] * ip;  // 0 after a breakdown
-    __syncwarp();
-    if (c > j && c < bs) {
-      const double ajc = a[j][c];
-      for (int r = j + 1; r <= c; ++r) a[r][c] -= a[j][r] * ajc;
-    }
-    __syncwarp();
   }
-  for (int r = 0; r < bs; ++r)
-    if (c < bs && c >= r) R[(int64_t)(o + r) * l + o + c] = a[r][c];
-  // column c of the block's inverse by back substitution (zero column after a breakdown)
-  double x[kCholB];
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r) x[r] = 0.0;
-  if (c < bs) {
-    x[c] = rinv[c];
-    for (int r = c - 1; r >= 0; --r) {
-      double acc = 0.0;
-      for (int q = r + 1; q <= c; ++q) acc += a[r][q] * x[q];
-      x[r] = -rinv[r] * acc;
-    }
+  for (int r = 0; r < kCholB; ++r)
+    if (c < bs && r <= c) R[(int64_t)(o + r) * l + o + c] = a[r];
+  // column c of the block's inverse X (R X = I) by back substitution over all columns at once:
+  // for p descending, x[p] = (delta_pc - acc[p]) / R[p][p], then acc[r] += R[r][p] x[p] for
+  // r < p, with R[r][p] broadcast from lane p; a zero pivot gives a zero row and column
+  double acc[kCholB];
+#pragma unroll
+  for (int r = 0; r < kCholB; ++r) acc[r] = 0.0;
+#pragma unroll
+  for (int p = kCholB - 1; p >= 0; --p) {
+    const double xp = ((c == p ? 1.0 : 0.0) - acc[p]) * rinv[p];
+    acc[p] = xp;
+#pragma unroll
+    for (int r = 0; r < p; ++r) acc[r] = fma(__shfl_sync(0xffffffffu, a[r], p), xp, acc[r]);
   }
   double* D = Dall + (int64_t)sg * kCholB * kCholB;
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r) D[r * kCholB + c] = x[r];
+  for (int r = 0; r < kCholB; ++r) D[r * kCholB + c] = c < bs ? acc[r] : 0.0;
 }
 
 // Block row k to the right of the diagonal block: R[o+t][j] = sum_{s <= t} D[s][t] R[o+s][j]
@@ -238,9 +239,61 @@ __global__ void k_chol_update(const int* __restrict__ segl, int lfix, int k, int
   R[(int64_t)i * l + j] -= acc;
 }
 
-// Ri = R^-1 column by column, one warp per column: x[c] = 1/R[c][c], then for r < c
-// x[r] = -(1/R[r][r]) sum_{r < p <= c} R[r][p] x[p] (lanes split the sum); a zero pivot gives
-// a zero row of R and a zero column of Ri. ri32 (optional) gets an FP32 copy.
+// Ri = R^-1 column by column, one warp per column. With the factor staged in shared memory
+// (l <= kTriSmemL): for p from c down to 0, x[p] = (delta_pc - acc[p]) / R[p][p], then
+// acc[r] += R[r][p] x[p] for all r < p at once (lanes split r), so the chain of c steps has no
+// reduction in it. Larger l reads R from global memory by rows: x[r] = -(1/R[r][r])
+// sum_{r < p <= c} R[r][p] x[p] with the lanes splitting the sum. A zero pivot gives a zero
+// row of R and a zero column of Ri. ri32 (optional) gets an FP32 copy.
+constexpr int kTriSmemL = 160;
+constexpr int kTriWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTriWarps) k_tri_inv_smem(
+    const int* __restrict__ segl, int lfix, const double* __restrict__ Rall, int64_t rseg,
+    double* __restrict__ Riall, float* __restrict__ ri32all, int64_t ldr32, int64_t r32seg) {
+  extern __shared__ double tri_smem[];
+  const int sg = blockIdx.y;
+  const int l = segl ? segl[sg] : lfix;
+  const int c0 = blockIdx.x * kTriWarps;
+  if (c0 >= l) return;
+  const int cmax = min(l - 1, c0 + kTriWarps - 1);  // last column of this CTA
+  const int ls = (cmax + 1) | 1;  // odd row stride: a column read by 32 lanes takes 2 wavefronts
+  double* Rs = tri_smem;                             // rows 0..cmax, columns 0..cmax
+  double* rinv = Rs + (int64_t)(cmax + 1) * ls;      // [cmax + 1]
+  double* accs = rinv + (cmax + 1);                  // per warp: [cmax + 1]
+  const double* R = Rall + sg * rseg;
+  for (int q = threadIdx.x; q < (cmax + 1) * (cmax + 1); q += blockDim.x) {
+    const int r = q / (cmax + 1), p = q - r * (cmax + 1);
+    if (p >= r) Rs[r * ls + p] = R[(int64_t)r * l + p];
+  }
+  for (int r = threadIdx.x; r <= cmax; r += blockDim.x) {
+    const double d = R[(int64_t)r * l + r];
+    rinv[r] = d > 0.0 ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = c0 + warp;
+  if (c > cmax) return;  // whole warps; no block barrier follows
+  double* Ri = Riall + sg * rseg;
+  float* ri32 = ri32all ? ri32all + sg * r32seg : nullptr;
+  double* acc = accs + warp * (cmax + 1);
+  for (int r = lane; r <= c; r += 32) acc[r] = 0.0;
+  for (int r = c + 1 + lane; r < l; r += 32) {
+    Ri[(int64_t)r * l + c] = 0.0;
+    if (ri32) ri32[(int64_t)r * ldr32 + c] = 0.f;
+  }
+  __syncwarp();
+  for (int p = c; p >= 0; --p) {
+    const double xp = ((p == c ? 1.0 : 0.0) - acc[p]) * rinv[p];
+    if (lane == 0) {
+      Ri[(int64_t)p * l + c] = xp;
+      if (ri32) ri32[(int64_t)p * ldr32 + c] = (float)xp;
+    }
+    for (int r = lane; r < p; r += 32) acc[r] = fma(Rs[r * ls + p], xp, acc[r]);
+    __syncwarp();
+  }
+}
+
 __global__ void k_tri_inv_cols(const int* __restrict__ segl, int lfix, const double* __restrict__ Rall,
                                int64_t rseg, double* __restrict__ Riall, float* __restrict__ ri32all,
                                int64_t ldr32, int64_t r32seg) {
@@ -305,11 +358,21 @@ static int chol_inv(int nseg, const int* segl, int lmax, const double* G, int64_
         segl, lmax, k, m, R, rseg);
     note_launch();
   }
-  const int wpb = 4;  // columns (warps) per CTA
-  const size_t smem = sizeof(double) * wpb * (size_t)lmax;
-  ABG_TRY(raise_smem_limit((const void*)k_tri_inv_cols, smem));
-  k_tri_inv_cols<<<dim3((unsigned)ceil_div(lmax, wpb), (unsigned)nseg), 32 * wpb, smem, s>>>(
-      segl, lmax, R, rseg, Ri, ri32, ldr32, r32seg);
+  if (lmax <= kTriSmemL) {
+    // the last CTA stages the most: rows and columns 0..lmax-1 (stride lmax + 1), plus 1/R[p][p]
+    // and one accumulator row per warp
+    const size_t smem =
+        sizeof(double) * ((size_t)lmax * (lmax + 1) + (size_t)lmax * (1 + kTriWarps));
+    ABG_TRY(raise_smem_limit((const void*)k_tri_inv_smem, smem));
+    k_tri_inv_smem<<<dim3((unsigned)ceil_div(lmax, kTriWarps), (unsigned)nseg), 32 * kTriWarps,
+                     smem, s>>>(segl, lmax, R, rseg, Ri, ri32, ldr32, r32seg);
+  } else {
+    const int wpb = 4;  // columns (warps) per CTA
+    const size_t smem = sizeof(double) * wpb * (size_t)lmax;
+    ABG_TRY(raise_smem_limit((const void*)k_tri_inv_cols, smem));
+    k_tri_inv_cols<<<dim3((unsigned)ceil_div(lmax, wpb), (unsigned)nseg), 32 * wpb, smem, s>>>(
+        segl, lmax, R, rseg, Ri, ri32, ldr32, r32seg);
+  }
   note_launch();
   ABG_LAUNCH_CHECK();
   return ABG_OK;

@@ -886,12 +886,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// TN without a raw staging ring: the transposing warps read their 4 x 4 blocks of A and B
-// straight from global memory (16-byte loads, 128-byte row segments per warp), so shared
-// memory holds only the operand sets and two of them fit at K = 256: the split of block
-// b + 1 overlaps the MMAs of block b. Two TMEM accumulators alternate between chunks, so the
+// TN with per-thread staging: each transposing thread copies its own 4 x 4 blocks of A and B
+// for the next row block into a private slot of shared memory with cp.async (16-byte copies,
+// zero-filled outside the block), and transposes + splits the current block from the other
+// slot into the operand set. An mbarrier arrival has release semantics and would wait for
+// loads still in flight into registers; cp.async copies are outside that ordering, so the
+// next block's copies stay in flight across the hand-off to the MMAs. Two operand sets when
+// they fit (K <= 128), else one. Two TMEM accumulators alternate between chunks, so the
 // partial of one chunk drains while the next accumulates.
-//   warp 0: TMEM owner + MMA issuer   warps 1..TW: load, transpose, split
+//   warp 0: TMEM owner + MMA issuer   warps 1..TW: copy, transpose, split
 //   warps TW+1..TW+4: epilogue (chunk partials to global, FP32)
 // ---------------------------------------------------------------------------
 constexpr int kTn2Units = 3;  // 4 x 4 blocks per transposing thread and row block
@@ -910,10 +913,24 @@ struct Tn2Args {
   float* part;     // [chunk][K][N]
   int nops;
   uint32_t op_bytes;
-  uint32_t acc_cols;  // TMEM columns of one accumulator (>= mblk * Np)
+  uint32_t stage_bytes;  // one staging slot: transposing threads x units x 64 bytes
+  uint32_t acc_cols;     // TMEM columns of one accumulator (>= mblk * Np)
   uint32_t tmem_cols;
   int* wait_err;
 };
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // 13 warps put four on one SM sub-partition, whose 16K registers allow 128 a thread
 template <int TW>
@@ -926,7 +943,8 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NO = p.nops;
   unsigned char* ops = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NO * p.op_bytes);
+  unsigned char* stage = smem + (size_t)NO * p.op_bytes;  // two staging slots
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 2 * (size_t)p.stage_bytes);
   const uint32_t opfull0 = smem_addr(bars), opempty0 = opfull0 + 8 * NO,
                  tfull0 = opempty0 + 8 * NO, tempty0 = tfull0 + 16, drain = tempty0 + 16;
   const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128, b_hi_bytes = (uint32_t)p.Np * 128;
@@ -1014,17 +1032,6 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
     int os = 0;
     uint32_t op_ph = 0;
     int64_t n = 0;
-    // one 4 x 4 block: rows m0..m0+3 of the chunk block, columns c0..c0+3 of src, as four
-    // float4 row loads (zero outside the block's valid rows and beyond the width lim)
-    auto load4 = [&](const float* src, int64_t ld, int lim, int c0, int m0, int mvalid,
-                     float4 (&v)[4]) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = m0 + e;
-        v[e] = (c0 < lim && m < mvalid) ? ld_nc_f4(src + (int64_t)m * ld + c0)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    };
     auto store4 = [&](const float4 (&v)[4], int c0, int k4, int lim, unsigned char* hi,
                       unsigned char* lo) {
 #pragma unroll
@@ -1052,10 +1059,13 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
         *reinterpret_cast<float4*>(lo + off) = lw;
       }
     };
-    // units: (column group c4, row group k4); a warp covers 8 column groups x 4 row groups.
+    // units: (column group c4, row group k4); a warp covers 4 column groups x all 8 row
+    // groups, lane l taking row group l & 7. A 16-byte shared store is served eight lanes at
+    // a time, and those eight then hold the same column and eight row groups: eight
+    // different 16-byte chunks of the 128-byte swizzle row, no bank conflict.
     // A thread's units are the same for every block; which block they read changes.
     const uint32_t na4 = a_rows / 4, nb4 = (uint32_t)p.Np / 4;
-    const uint32_t ua = ((na4 + 7) / 8) * 64, ub = ((nb4 + 7) / 8) * 64;
+    const uint32_t ua = ((na4 + 3) / 4) * 32, ub = ((nb4 + 3) / 4) * 32;
     constexpr int kMaxU = kTn2Units;  // units per thread (A and B together), checked at launch
     int uc0[kMaxU], uk4[kMaxU], uwhich[kMaxU];
 #pragma unroll
@@ -1068,37 +1078,46 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
         const bool isA = u < ua;
         const uint32_t uu = isA ? u : u - ua;
         const uint32_t g = uu >> 5, l = uu & 31;
-        const uint32_t c4 = 8 * (g >> 1) + (l & 7);
+        const uint32_t c4 = 4 * g + (l >> 3);
         if (c4 < (isA ? na4 : nb4)) {
           uwhich[q] = isA ? 0 : 1;
           uc0[q] = (int)(4 * c4);
-          uk4[q] = (int)(4 * (g & 1) + (l >> 3));
+          uk4[q] = (int)(l & 7);
         }
       }
     }
     auto nblocks = [&](int64_t c) { return (p.chunk_rows[c] + kTnRows - 1) / kTnRows; };
-    // the loads of slot q of block b of chunk c into registers (issued, not waited for)
-    auto issue = [&](float4 (&v)[4], int q, int64_t c, int b) {
+    // this thread's 16-byte pieces of block b of chunk c into staging slot sl: unit q, row e
+    // at ((q * 4 + e) * kT + t) * 16, zero-filled outside the block's rows or the width
+    const uint32_t stage0 = smem_addr(stage);
+    auto issue = [&](int sl, int64_t c, int b) {
       const int sg = p.chunk_seg[c];
       const int mvalid = p.chunk_rows[c] - b * kTnRows;
       const int64_t row0 = p.chunk_row0[c] + (int64_t)b * kTnRows;
-      if (uwhich[q] == 0)
-        load4(p.A + row0 * p.lda, p.lda, p.segK ? p.segK[sg] : p.K, uc0[q], 4 * uk4[q], mvalid,
-              v);
-      else if (uwhich[q] == 1)
-        load4(p.B + row0 * p.ldb, p.ldb, p.segN ? p.segN[sg] : p.N, uc0[q], 4 * uk4[q], mvalid,
-              v);
-    };
-    // One register set, rolled: right after slot q of block b is transposed into its operand
-    // set, slot q of the thread's next block is loaded into the same registers, so every load
-    // has one whole block period to arrive.
-    float4 v[kMaxU][4];
-    int64_t c = blockIdx.x;
-    int b = 0;
-    if (c < n_chunks) {
+      const int Ks = p.segK ? p.segK[sg] : p.K;
+      const int Ns = p.segN ? p.segN[sg] : p.N;
 #pragma unroll
-      for (int q = 0; q < kMaxU; ++q) issue(v[q], q, c, 0);
-    }
+      for (int q = 0; q < kMaxU; ++q) {
+        if (uwhich[q] < 0) continue;
+        const bool isA = uwhich[q] == 0;
+        const float* src = isA ? p.A + row0 * p.lda : p.B + row0 * p.ldb;
+        const int64_t ld = isA ? p.lda : p.ldb;
+        const int lim = isA ? Ks : Ns;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int m = 4 * uk4[q] + e;
+          const bool ok = uc0[q] < lim && m < mvalid;
+          const uint32_t dst = stage0 + (uint32_t)sl * p.stage_bytes +
+                               (uint32_t)(((q * 4 + e) * kT + t) * 16);
+          cp_async16(dst, ok ? (const void*)(src + (int64_t)m * ld + uc0[q]) : (const void*)p.A,
+                     ok ? 16u : 0u);
+        }
+      }
+    };
+    int64_t c = blockIdx.x;
+    int b = 0, sl = 0;
+    if (c < n_chunks) issue(0, c, 0);
+    cp_async_commit();
     while (c < n_chunks && !bad) {
       int64_t c2 = c;
       int b2 = b;
@@ -1106,7 +1125,9 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
         c2 += gridDim.x;
         b2 = 0;
       }
-      const bool more = c2 < n_chunks;
+      if (c2 < n_chunks) issue(sl ^ 1, c2, b2);
+      cp_async_commit();
+      cp_async_wait<1>();  // this block's copies have landed (the next block's may not)
       const bool ok = n < NO || mbar_wait_bounded(opempty0 + 8 * os, op_ph ^ 1u);
       if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
         bad = true;
@@ -1116,13 +1137,17 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
       const int Ks = p.segK ? p.segK[sg] : p.K;
       const int Ns = p.segN ? p.segN[sg] : p.N;
       unsigned char* o = ops + (size_t)os * p.op_bytes;
+      const float4* st = reinterpret_cast<const float4*>(stage + (size_t)sl * p.stage_bytes);
 #pragma unroll
       for (int q = 0; q < kMaxU; ++q) {
+        if (uwhich[q] < 0) continue;
+        float4 v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = st[(q * 4 + e) * kT + t];
         if (uwhich[q] == 0)
-          store4(v[q], uc0[q], uk4[q], Ks, o, o + a_hi_bytes);
-        else if (uwhich[q] == 1)
-          store4(v[q], uc0[q], uk4[q], Ns, o + 2 * a_hi_bytes, o + 2 * a_hi_bytes + b_hi_bytes);
-        if (more) issue(v[q], q, c2, b2);
+          store4(v, uc0[q], uk4[q], Ks, o, o + a_hi_bytes);
+        else
+          store4(v, uc0[q], uk4[q], Ns, o + 2 * a_hi_bytes, o + 2 * a_hi_bytes + b_hi_bytes);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMAs
       warp_arrive(opfull0 + 8 * os);
@@ -1133,7 +1158,9 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
       ++n;
       c = c2;
       b = b2;
+      sl ^= 1;
     }
+    cp_async_wait<0>();  // no copy in flight when the CTA leaves
   } else {
     // epilogue: accumulator rows (the K index) -> partial rows, N columns
     const int quad = warp & 3;
@@ -1747,9 +1774,11 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.mblk = (int)ceil_div(a.K, kTcM);
   if (p.Np > 128 || p.mblk > 2) return ABG_OK;
   // units per transposing thread: A (mblk 128 / 4 column groups) and B (Np / 4), x 8 row
-  // groups, in warps of 8 column groups (k_tc_tn2 holds at most kTn2Units per thread)
-  const int64_t units = ceil_div(p.mblk * kTcM / 4, 8) * 64 + ceil_div(p.Np / 4, 8) * 64;
+  // groups, in warps of 4 column groups (k_tc_tn2 holds at most kTn2Units per thread)
+  const int64_t units = ceil_div(p.mblk * kTcM / 4, 4) * 32 + ceil_div(p.Np / 4, 4) * 32;
   if (units > kTn2Units * 32 * TW) return ABG_OK;
+  const int U = (int)ceil_div(units, 32 * TW);  // units per transposing thread
+  p.stage_bytes = 32u * TW * (uint32_t)U * 64u;
   ABG_TRY(current_flag(&p.wait_err));
   p.A = a.A;
   p.lda = a.lda;
@@ -1767,11 +1796,11 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.tmem_cols = 2 * p.acc_cols;
   if (p.tmem_cols > 512) return ABG_OK;
   size_t smem = 0;
-  for (p.nops = 4; p.nops >= 2; --p.nops) {
-    smem = 1024 + (size_t)p.nops * p.op_bytes + 8 * (2 * p.nops + 5);
+  for (p.nops = 2; p.nops >= 1; --p.nops) {
+    smem = 1024 + (size_t)p.nops * p.op_bytes + 2 * (size_t)p.stage_bytes + 8 * (2 * p.nops + 5);
     if (smem <= 220 * 1024) break;
   }
-  if (p.nops < 2) return ABG_OK;
+  if (p.nops < 1) return ABG_OK;
   ABG_TRY(raise_smem_limit((const void*)k_tc_tn2<TW>, smem));
   const unsigned grid = (unsigned)std::min<int64_t>(rs.n_chunks, num_sms());
   k_tc_tn2<TW><<<grid, 32 * (TW + 5), smem, s>>>(p, rs.n_chunks);
