@@ -138,8 +138,8 @@ __global__ void k_chol_init(const int* __restrict__ segl, int lfix, const double
 
 // Diagonal block k of each segment (one warp): factor in place, and its upper-triangular
 // inverse into D_s (32 x 32, row stride 32). Lane c holds column c of the block in registers;
-// every lane computes each pivot's square root and reciprocal itself (no serial lane), and
-// row j of the factor reaches the other lanes by shuffles.
+// every lane computes each pivot's reciprocal square root itself (no serial lane), and row j
+// of the factor reaches the other lanes by shuffles.
 __global__ void __launch_bounds__(32) k_chol_diag(const int* __restrict__ segl, int lfix, int k,
                                                   double* __restrict__ Rall, int64_t rseg,
                                                   const double* __restrict__ tol,
@@ -163,8 +163,11 @@ __global__ void __launch_bounds__(32) k_chol_diag(const int* __restrict__ segl, 
     if (j < bs) {  // uniform over the warp
       const double pv = __shfl_sync(0xffffffffu, a[j], j);
       const bool ok = pv > t;
-      const double sq = ok ? sqrt(pv) : 0.0;
-      const double ip = ok ? 1.0 / sq : 0.0;
+      // one reciprocal square root gives both the pivot (pv / sqrt(pv)) and its inverse: FP64
+      // runs on a narrow unit per SM sub-partition, and this chain is serial over the pivots
+      const double rs = ok ? rsqrt(pv) : 0.0;
+      const double sq = pv * rs;
+      const double ip = rs;
       if (!ok && c == 0) atomicAdd(breakdowns, 1);
       rinv[j] = ip;
       a[j] = c == j ? sq : (c > j ? a[j] * ip : a[j]);  // row j (0 after a breakdown)

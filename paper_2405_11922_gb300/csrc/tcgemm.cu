@@ -114,6 +114,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       : "memory");
 }
 
+// the same MMA with A (128 lanes x 8 tf32 columns) read from tensor memory
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // instruction descriptor: D f32, A/B bf16, M = 128, N = n; a_mn / b_mn: operand is MN-major
 __host__ __device__ constexpr uint32_t bf16_idesc(int n, bool a_mn, bool b_mn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
@@ -194,6 +205,33 @@ __global__ void k_tc_prep_b(const float* __restrict__ B, int64_t ldb, int64_t b_
     bhi[o] = h;
     blo[o] = l;
   }
+}
+
+// 16 / 32 consecutive 32-bit columns of this thread's TMEM lane from registers (complete after
+// tmem_wait_st)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // 32 consecutive fp32 columns of this thread's TMEM lane, without waiting: the registers are
@@ -420,7 +458,11 @@ __device__ void tc_epilogue_sincos(const TcArgs& p, uint32_t tacc, int quad, int
 // MODE 0: C = acc with the elementwise epilogues; 1: NCI argmax; 2: random features (sin/cos
 // and column sums). SPLITW warps split A; EPIG groups of four epilogue warps take the tiles of
 // alternate accumulator buffers (group g: buffer g), so a slow epilogue keeps up with the MMAs.
-template <int MODE, int SPLITW, int EPIG>
+// ATM (N <= 128): the split warps write A's hi and lo parts into tensor memory (one 64-column
+// slot per stage after the two 128-column accumulators) and the MMAs read A from there, so
+// shared memory carries A once (TMA in, split warps out) instead of three more times (the
+// split's two writes and the MMAs' reads of hi and lo).
+template <int MODE, int SPLITW, int EPIG, bool ATM>
 __global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
     k_tc_nn(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bhi_map,
             const __grid_constant__ CUtensorMap blo_map, const TcArgs p, int64_t n_tiles) {
@@ -460,7 +502,9 @@ __global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t acc_cols = p.tmem_cols / 2;  // columns of one accumulator buffer
+  const uint32_t acc_cols = ATM ? 128u : p.tmem_cols / 2;  // columns of one accumulator buffer
+  const uint32_t a_tm0 = tmem + 2 * acc_cols;                // ATM: A slot of stage s at + 64 s
+  const uint32_t boff = (ATM ? 1u : 2u) * kTcABytes;         // B_hi within a stage
   // after a wait has run out anywhere, later CTAs skip their work instead of waiting again
   bool bad = *reinterpret_cast<volatile int*>(p.wait_err) != 0;
 
@@ -480,9 +524,8 @@ __global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
           const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
           mbar_expect_tx(full0 + 8 * s, kTcABytes + 2 * p.b_bytes);
           tma_load_2d(st, &amap, kb * kTcBK, row0, full0 + 8 * s);
-          tma_load_2d(st + 2 * kTcABytes, &bhi_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
-          tma_load_2d(st + 2 * kTcABytes + p.b_bytes, &blo_map, kb * kTcBK, sg * p.Np,
-                      full0 + 8 * s);
+          tma_load_2d(st + boff, &bhi_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
+          tma_load_2d(st + boff + p.b_bytes, &blo_map, kb * kTcBK, sg * p.Np, full0 + 8 * s);
           if (++s == S) {
             s = 0;
             ph ^= 1u;
@@ -511,15 +554,26 @@ __global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
           }
           tc_fence_after();
           const uint32_t st = smem_addr(smem + (size_t)s * p.stage_bytes);
-          const uint32_t a_hi = st, a_lo = st + kTcABytes, b_hi = st + 2 * kTcABytes,
-                         b_lo = b_hi + p.b_bytes;
+          const uint32_t b_hi = st + boff, b_lo = b_hi + p.b_bytes;
+          if constexpr (ATM) {
+            const uint32_t ta = a_tm0 + 64u * (uint32_t)s;  // hi: columns 0..31, lo: 32..63
 #pragma unroll
-          for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 32 bytes
-            const uint32_t off = 32u * j;
-            mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
-                     (kb | j) != 0);
-            mma_tf32(tacc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
-            mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 8 TMEM columns
+              const uint32_t off = 32u * j;
+              mma_tf32_ta(tacc, ta + 8u * j, sw128_desc(b_hi + off), idesc, (kb | j) != 0);
+              mma_tf32_ta(tacc, ta + 32u + 8u * j, sw128_desc(b_hi + off), idesc, 1u);
+              mma_tf32_ta(tacc, ta + 8u * j, sw128_desc(b_lo + off), idesc, 1u);
+            }
+          } else {
+            const uint32_t a_hi = st, a_lo = st + kTcABytes;
+#pragma unroll
+            for (int j = 0; j < kTcBK / 8; ++j) {  // UMMA K = 8 tf32 = 32 bytes
+              const uint32_t off = 32u * j;
+              mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
+                       (kb | j) != 0);
+              mma_tf32(tacc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+              mma_tf32(tacc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            }
           }
           mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
           if (++s == S) {
@@ -544,6 +598,47 @@ __global__ void __launch_bounds__(32 * (2 + SPLITW + 4 * EPIG), 1)
         if (__any_sync(0xffffffffu, !ok)) {  // the whole warp leaves together
           bad = true;
           break;
+        }
+        if constexpr (ATM) {
+          // this thread's tile row (its TMEM lane) and its share of the stage's 8 chunks; the
+          // 128-byte swizzle puts logical chunk j of row r at physical chunk j ^ (r & 7), so
+          // eight lanes in a row read eight different chunks
+          constexpr int kCh = SPLITW >= 8 ? 4 : 8;
+          const int quad = warp & 3, r = 32 * quad + lane;
+          const int j0 = SPLITW >= 8 ? ((warp - 2) >> 2) * kCh : 0;
+          const unsigned char* arow = smem + (size_t)s * p.stage_bytes + (size_t)r * 128;
+          uint32_t hv[4 * kCh], lv[4 * kCh];
+#pragma unroll
+          for (int c = 0; c < kCh; ++c) {
+            const int j = j0 + c;
+            const float4 v = *reinterpret_cast<const float4*>(arow + ((j ^ (r & 7)) * 16));
+            const int k0 = kb * kTcBK + 4 * j;
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float h = k0 + e < Ks ? rna_tf32(x[e]) : 0.f;
+              const float l = k0 + e < Ks ? rna_tf32(x[e] - h) : 0.f;
+              hv[4 * c + e] = __float_as_uint(h);
+              lv[4 * c + e] = __float_as_uint(l);
+            }
+          }
+          const uint32_t ta = a_tm0 + ((uint32_t)(32 * quad) << 16) + 64u * (uint32_t)s +
+                              (uint32_t)(4 * j0);
+          if constexpr (kCh == 4) {
+            tmem_st16(ta, hv);
+            tmem_st16(ta + 32u, lv);
+          } else {
+            tmem_st32(ta, hv);
+            tmem_st32(ta + 32u, lv);
+          }
+          tmem_wait_st();
+          tc_fence_before();  // the MMAs read these columns after the barrier
+          warp_arrive(split0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+          }
+          continue;
         }
         float4* a = reinterpret_cast<float4*>(smem + (size_t)s * p.stage_bytes);
         float4* alo = a + kTcABytes / 16;
@@ -1653,6 +1748,15 @@ int tc_wait_flag(cudaStream_t s, int* flag) {
   return ABG_OK;
 }
 
+// ABG_TC_A_TMEM=0 keeps A in shared memory (the layout before A moved to tensor memory)
+static bool a_tmem_off() {
+  static const bool off = [] {
+    const char* e = std::getenv("ABG_TC_A_TMEM");
+    return e && e[0] == '0';
+  }();
+  return off;
+}
+
 int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   static_assert(kTile == kTcM, "row-space tiles must match the UMMA M");
   *used = false;
@@ -1732,11 +1836,17 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   p.in_scale = a.in_scale;
   p.out_scale = a.out_scale;
   p.colsum = a.colsum_part;
+  // A in tensor memory when two 128-column accumulators leave room for the A slots
+  const bool atm = Np <= 128 && !a_tmem_off();
   p.b_bytes = (uint32_t)Np * kTcBK * 4;
-  p.stage_bytes = 2 * kTcABytes + 2 * p.b_bytes;  // multiple of 1024
+  p.stage_bytes = (atm ? 1 : 2) * kTcABytes + 2 * p.b_bytes;  // multiple of 1024
   p.stages = (int)std::max<int64_t>(2, std::min<int64_t>(4, (200 * 1024) / p.stage_bytes));
-  p.tmem_cols = 64;  // two accumulator buffers of a power of two >= 32 columns each
-  while ((int)p.tmem_cols < 2 * Np) p.tmem_cols *= 2;
+  if (atm) {
+    p.tmem_cols = 512;  // accumulators at 0 and 128, A slots of 64 columns from 256
+  } else {
+    p.tmem_cols = 64;  // two accumulator buffers of a power of two >= 32 columns each
+    while ((int)p.tmem_cols < 2 * Np) p.tmem_cols *= 2;
+  }
   // stages, alignment slack, barriers, and for the sin/cos epilogue its column-sum scratch
   const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 +
                       round_up(8 * (3 * p.stages + 4), 16) +
@@ -1746,15 +1856,17 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   // groups); the plain products are bound by the tf32 split (eight split warps); the sin/cos
   // epilogue's registers leave room for the base layout only
   const unsigned grid = (unsigned)std::min<int64_t>(rs.n_tiles, num_sms());
+  auto launch = [&](auto kern, int warps) -> int {
+    ABG_TRY(raise_smem_limit((const void*)kern, smem));
+    kern<<<grid, 32 * warps, smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+    return ABG_OK;
+  };
   if (a.argmax) {
-    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<1, 4, 2>, smem));
-    k_tc_nn<1, 4, 2><<<grid, 32 * (2 + 4 + 8), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+    ABG_TRY(atm ? launch(k_tc_nn<1, 4, 2, true>, 14) : launch(k_tc_nn<1, 4, 2, false>, 14));
   } else if (a.sincos) {
-    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<2, 4, 1>, smem));
-    k_tc_nn<2, 4, 1><<<grid, 32 * (2 + 4 + 4), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+    ABG_TRY(atm ? launch(k_tc_nn<2, 4, 1, true>, 10) : launch(k_tc_nn<2, 4, 1, false>, 10));
   } else {
-    ABG_TRY(raise_smem_limit((const void*)k_tc_nn<0, 8, 1>, smem));
-    k_tc_nn<0, 8, 1><<<grid, 32 * (2 + 8 + 4), smem, s>>>(amap, hmap, lmap, p, rs.n_tiles);
+    ABG_TRY(atm ? launch(k_tc_nn<0, 8, 1, true>, 14) : launch(k_tc_nn<0, 8, 1, false>, 14));
   }
   note_launch();
   note_tc_launch();
