@@ -136,67 +136,96 @@ __global__ void k_chol_init(const int* __restrict__ segl, int lfix, const double
   }
 }
 
-// Diagonal block k of each segment (one warp): factor in place, and its upper-triangular
-// inverse into D_s (32 x 32, row stride 32). Lane c holds column c of the block in registers;
-// every lane computes each pivot's reciprocal square root itself (no serial lane), and row j
-// of the factor reaches the other lanes by shuffles.
-__global__ void __launch_bounds__(32) k_chol_diag(const int* __restrict__ segl, int lfix, int k,
-                                                  double* __restrict__ Rall, int64_t rseg,
-                                                  const double* __restrict__ tol,
-                                                  double* __restrict__ Dall,
-                                                  int* __restrict__ breakdowns) {
+// Diagonal block k of each segment (one CTA of four warps): factor in place, and its
+// upper-triangular inverse into D_s (32 x 32, row stride 32). Warp w holds rows w, w + 4, ...
+// of the block in registers (lane c = column c), so the FP64 work of every pivot is spread
+// over the SM's four sub-partitions: the owner of row j turns it into row j of the factor
+// (one reciprocal square root gives the pivot and its inverse) and publishes it in shared
+// memory, then every warp updates its rows below j. Each warp updates its rows in ascending
+// order, so the next pivot's owner has its row ready first. The inverse X (R X = I) is a back
+// substitution over all columns at once: for p descending the owner of row p finishes it,
+// x[p] = (delta_pc - acc[p]) / R[p][p], publishes it, and every warp adds R[r][p] x[p] to its
+// rows r < p. Pivot and solved rows alternate between two shared buffers, so one barrier per
+// step orders them.
+constexpr int kCholW = 4;                 // warps per diagonal block
+constexpr int kCholR = kCholB / kCholW;  // rows per warp
+
+__global__ void __launch_bounds__(32 * kCholW) k_chol_diag(const int* __restrict__ segl, int lfix,
+                                                           int k, double* __restrict__ Rall,
+                                                           int64_t rseg,
+                                                           const double* __restrict__ tol,
+                                                           double* __restrict__ Dall,
+                                                           int* __restrict__ breakdowns) {
+  __shared__ double row[2][kCholB];  // the pivot row (factor) / the solved row (inverse)
+  __shared__ double rinv[kCholB];
   const int sg = blockIdx.x;
   const int l = segl ? segl[sg] : lfix;
   const int o = k * kCholB;
-  if (o >= l) return;
+  if (o >= l) return;  // whole CTA
   const int bs = min(kCholB, l - o);
   double* R = Rall + sg * rseg;
-  const int c = threadIdx.x;  // this lane's column of the block
-  double a[kCholB], rinv[kCholB];
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;  // this lane's column
+  double a[kCholR];  // rows w + 4 i of the block, column c
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r)
-    a[r] = (c < bs && r <= c) ? R[(int64_t)(o + r) * l + o + c] : 0.0;
+  for (int i = 0; i < kCholR; ++i) {
+    const int r = w + kCholW * i;
+    a[i] = (c < bs && r <= c) ? R[(int64_t)(o + r) * l + o + c] : 0.0;
+  }
   const double t = tol[sg];
 #pragma unroll
   for (int j = 0; j < kCholB; ++j) {
-    rinv[j] = 0.0;
-    if (j < bs) {  // uniform over the warp
-      const double pv = __shfl_sync(0xffffffffu, a[j], j);
+    if (j >= bs) {  // uniform over the CTA
+      if (threadIdx.x == 0) rinv[j] = 0.0;
+      continue;
+    }
+    if (w == j % kCholW) {
+      const int ij = j / kCholW;
+      const double pv = __shfl_sync(0xffffffffu, a[ij], j);
       const bool ok = pv > t;
-      // one reciprocal square root gives both the pivot (pv / sqrt(pv)) and its inverse: FP64
-      // runs on a narrow unit per SM sub-partition, and this chain is serial over the pivots
       const double rs = ok ? rsqrt(pv) : 0.0;
-      const double sq = pv * rs;
-      const double ip = rs;
       if (!ok && c == 0) atomicAdd(breakdowns, 1);
-      rinv[j] = ip;
-      a[j] = c == j ? sq : (c > j ? a[j] * ip : a[j]);  // row j (0 after a breakdown)
+      a[ij] = c == j ? pv * rs : (c > j ? a[ij] * rs : a[ij]);  // row j (0 after a breakdown)
+      row[j & 1][c] = a[ij];
+      if (c == 0) rinv[j] = rs;
+    }
+    __syncthreads();
 #pragma unroll
-      for (int r = j + 1; r < kCholB; ++r) {
-        const double rjr = __shfl_sync(0xffffffffu, a[j], r);  // R[j][r]
-        if (c >= r) a[r] = fma(-rjr, a[j], a[r]);
-      }
+    for (int i = 0; i < kCholR; ++i) {
+      const int r = w + kCholW * i;
+      if (r > j && c >= r) a[i] = fma(-row[j & 1][r], row[j & 1][c], a[i]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r)
-    if (c < bs && r <= c) R[(int64_t)(o + r) * l + o + c] = a[r];
-  // column c of the block's inverse X (R X = I) by back substitution over all columns at once:
-  // for p descending, x[p] = (delta_pc - acc[p]) / R[p][p], then acc[r] += R[r][p] x[p] for
-  // r < p, with R[r][p] broadcast from lane p; a zero pivot gives a zero row and column
-  double acc[kCholB];
+  for (int i = 0; i < kCholR; ++i) {
+    const int r = w + kCholW * i;
+    if (c < bs && r <= c) R[(int64_t)(o + r) * l + o + c] = a[i];
+  }
+  __syncthreads();  // rinv complete; the row buffers are free again
+  double x[kCholR];
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r) acc[r] = 0.0;
+  for (int i = 0; i < kCholR; ++i) x[i] = 0.0;
 #pragma unroll
   for (int p = kCholB - 1; p >= 0; --p) {
-    const double xp = ((c == p ? 1.0 : 0.0) - acc[p]) * rinv[p];
-    acc[p] = xp;
+    if (w == p % kCholW) {
+      const int ip = p / kCholW;
+      x[ip] = ((c == p ? 1.0 : 0.0) - x[ip]) * rinv[p];
+      row[p & 1][c] = x[ip];
+    }
+    __syncthreads();
+    const double xp = row[p & 1][c];
 #pragma unroll
-    for (int r = 0; r < p; ++r) acc[r] = fma(__shfl_sync(0xffffffffu, a[r], p), xp, acc[r]);
+    for (int i = 0; i < kCholR; ++i) {
+      const int r = w + kCholW * i;
+      const double rrp = __shfl_sync(0xffffffffu, a[i], p);  // R[r][p] (lane p of row r)
+      if (r < p) x[i] = fma(rrp, xp, x[i]);
+    }
   }
   double* D = Dall + (int64_t)sg * kCholB * kCholB;
 #pragma unroll
-  for (int r = 0; r < kCholB; ++r) D[r * kCholB + c] = c < bs ? acc[r] : 0.0;
+  for (int i = 0; i < kCholR; ++i) {
+    const int r = w + kCholW * i;
+    D[r * kCholB + c] = c < bs ? x[i] : 0.0;
+  }
 }
 
 // Block row k to the right of the diagonal block: R[o+t][j] = sum_{s <= t} D[s][t] R[o+s][j]
@@ -350,7 +379,8 @@ static int chol_inv(int nseg, const int* segl, int lmax, const double* G, int64_
   note_launch();
   const int nb = (int)ceil_div(lmax, kCholB);
   for (int k = 0; k < nb; ++k) {
-    k_chol_diag<<<(unsigned)nseg, 32, 0, s>>>(segl, lmax, k, R, rseg, tol, D, breakdowns);
+    k_chol_diag<<<(unsigned)nseg, 32 * kCholW, 0, s>>>(segl, lmax, k, R, rseg, tol, D,
+                                                     breakdowns);
     note_launch();
     const int m = lmax - (k + 1) * kCholB;  // trailing columns of the largest segment
     if (m <= 0) continue;
