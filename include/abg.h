@@ -130,7 +130,8 @@ typedef struct {
  *                         products, halving the bytes each gather reads. The
  *                         products accumulate in FP32 and Z_hat (the last
  *                         round, Eq. 2) is FP32.
- * options is 0 or ABG_REUSE_PROPAGATION: the solve may take Z_hat (Algorithm
+ * options is 0 or a combination of ABG_REUSE_PROPAGATION and ABG_WARM_START.
+ * ABG_REUSE_PROPAGATION: the solve may take Z_hat (Algorithm
  * 1: the propagation of Eq. 6 and the row normalisation of Eq. 2) from an
  * earlier solve on the same graph that had this option and the same alpha,
  * gamma, d and ABG_BF16_PROPAGATION bit (and, with d < d_u, the same seed,
@@ -141,13 +142,24 @@ typedef struct {
  * until abg_destroy or until a solve with other keys replaces it; it counts in
  * abg_graph_footprint). Labels and objective are bitwise those of a solve
  * without the option. Ignored for batches (abg_batch_create). Without the
- * option nothing is kept or reused. */
+ * option nothing is kept or reused.
+ * ABG_WARM_START (may be combined with the above; an option the paper does not
+ * have): a resident re-solve, e.g. with another alpha, starts the T_f ONMF
+ * steps of Algorithm 2 (Eqs. 16-17) from the Phi and H that an earlier solve
+ * on the same graph with this option and the same k and d ended them with,
+ * instead of the randomized-SVD seeding of Eq. 18 (which it skips). The result
+ * is that of the ONMF and NCI steps from that start, not the one of a cold
+ * solve. A solve with the option that finds no such factors seeds as usual and
+ * keeps its final Phi and H on the graph (n_u x round_up(k, 4) and
+ * 2d x round_up(k, 4) floats, held like Z_hat above and counted in
+ * abg_graph_footprint). Ignored for batches. */
 #define ABG_NCI_PROCRUSTES 1
 #define ABG_NCI_EARLY_STOP 2
 #define ABG_PRECISION_FP32 0
 #define ABG_BF16_CONTRACT 1
 #define ABG_BF16_PROPAGATION 2
 #define ABG_REUSE_PROPAGATION 1
+#define ABG_WARM_START 2
 typedef struct {
   int32_t k, gamma, d, t_f, t_g, oversample, power_iters;
   int32_t nci_flags;
@@ -175,6 +187,7 @@ typedef struct {
   float ms_phase[6];
   int32_t nci_passes;       /* NCI passes run (t_g unless ABG_NCI_EARLY_STOP)   */
   int32_t reused_propagation; /* 1: Z_hat came from an earlier solve (ABG_REUSE_PROPAGATION) */
+  int32_t warm_started;       /* 1: ONMF started from an earlier solve's Phi, H (ABG_WARM_START) */
 } abg_result;
 
 ABG_API const char* abg_strerror(int status);

@@ -45,7 +45,7 @@ class abg_result(C.Structure):
     _fields_ = [("objective", _f64), ("trace_obj", _f64), ("min_margin", _f64),
                 ("last_changes", _i32), ("empty_clusters", _i32), ("clamped_rows", _i32),
                 ("chol_breakdowns", _i32), ("ms_phase", C.c_float * 6), ("nci_passes", _i32),
-                ("reused_propagation", _i32)]
+                ("reused_propagation", _i32), ("warm_started", _i32)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "ms_phase" else getattr(self, f))
@@ -166,12 +166,14 @@ ABG_PRECISION_FP32 = 0
 ABG_BF16_CONTRACT = 1
 ABG_BF16_PROPAGATION = 2
 ABG_REUSE_PROPAGATION = 1
+ABG_WARM_START = 2
 
 
 def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5, t_g: int = 20,
            oversample: int = 10, power_iters: int = 4, seed: int = 0, procrustes: bool = False,
            early_stop: bool = False, bf16_propagation: bool = False,
-           bf16_contract: bool = False, reuse_propagation: bool = False) -> abg_params:
+           bf16_contract: bool = False, reuse_propagation: bool = False,
+           warm_start: bool = False) -> abg_params:
     p = abg_params()
     lib().abg_params_default(C.byref(p))
     p.k, p.alpha, p.gamma, p.d, p.t_f, p.t_g = k, alpha, gamma, d, t_f, t_g
@@ -179,7 +181,8 @@ def params(k: int, alpha: float = 0.6, gamma: int = 6, d: int = 0, t_f: int = 5,
     p.nci_flags = (ABG_NCI_PROCRUSTES if procrustes else 0) | (ABG_NCI_EARLY_STOP if early_stop else 0)
     p.precision = ((ABG_BF16_PROPAGATION if bf16_propagation else 0) |
                    (ABG_BF16_CONTRACT if bf16_contract else 0))
-    p.options = ABG_REUSE_PROPAGATION if reuse_propagation else 0
+    p.options = ((ABG_REUSE_PROPAGATION if reuse_propagation else 0) |
+                 (ABG_WARM_START if warm_start else 0))
     return p
 
 

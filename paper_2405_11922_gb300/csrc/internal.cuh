@@ -59,6 +59,7 @@ struct abg_graph {
   // Z_hat kept by a solve with ABG_REUSE_PROPAGATION (one at a time; see pipeline.cu)
   std::mutex zmu;
   std::shared_ptr<struct ZCache> zcache;
+  std::shared_ptr<struct PhiCache> phicache;  // final Phi, H of a solve with ABG_WARM_START
   int64_t footprint = 0;
   void* blocks[64] = {};
   int n_blocks = 0;

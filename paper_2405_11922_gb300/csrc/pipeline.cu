@@ -32,6 +32,23 @@ struct ZCache {
   }
 };
 
+// Phi and H at the end of the ONMF steps of a solve with ABG_WARM_START, for a later solve
+// on the same graph with the same k and d (the shapes that fix them).
+struct PhiCache {
+  int k = 0, d = 0;
+  int device = 0;
+  float* phi = nullptr;  // n_u x round_up(k, 4)
+  float* h = nullptr;    // 2d x round_up(k, 4)
+  int64_t phi_bytes = 0, h_bytes = 0;
+  cudaEvent_t ready = nullptr;  // recorded after the copies into phi and h
+  ~PhiCache() {
+    cudaSetDevice(device);
+    if (ready) cudaEventDestroy(ready);
+    if (phi) cudaFree(phi);  // the last solve that read them has finished (it held a reference)
+    if (h) cudaFree(h);
+  }
+};
+
 using namespace abg;
 
 namespace {
@@ -62,7 +79,8 @@ int abg::check_params(const abg_graph* g, const abg_params* p, int64_t n_rows, i
             "unknown nci_flags %d", p->nci_flags);
   ABG_CHECK((p->precision & ~(ABG_BF16_CONTRACT | ABG_BF16_PROPAGATION)) == 0,
             "unknown precision %d", p->precision);
-  ABG_CHECK((p->options & ~ABG_REUSE_PROPAGATION) == 0, "unknown options %d", p->options);
+  ABG_CHECK((p->options & ~(ABG_REUSE_PROPAGATION | ABG_WARM_START)) == 0, "unknown options %d",
+            p->options);
   *d_eff = d;
   return ABG_OK;
 }
@@ -73,6 +91,8 @@ namespace {
 struct SolveOut {
   int reused = 0;                     // Z_hat taken from the graph's ZCache
   std::shared_ptr<ZCache> zhold;      // keeps that ZCache alive until the solve has finished
+  int warm = 0;                       // Phi, H taken from the graph's PhiCache
+  std::shared_ptr<PhiCache> phold;    // keeps that PhiCache alive until the solve has finished
   int32_t* labels = nullptr;   // rows
   double* obj = nullptr;       // 2 per segment
   int* counters = nullptr;     // 3 per segment: changes, min margin bits, empty clusters
@@ -263,6 +283,32 @@ int zcache_store(abg_graph* g, const ZKey& key, const float* zhat, int64_t count
   return ABG_OK;
 }
 
+// Keeps copies of phi (n_u x ldp floats) and h (2d x ldp) on g for later warm-started solves
+// with the same k and d, replacing those held before. Best effort, as zcache_store.
+int phicache_store(abg_graph* g, int k, int d, const float* phi, int64_t phi_count,
+                   const float* h, int64_t h_count, cudaStream_t s) {
+  auto c = std::make_shared<PhiCache>();
+  c->k = k;
+  c->d = d;
+  c->device = g->device;
+  c->phi_bytes = phi_count * (int64_t)sizeof(float);
+  c->h_bytes = h_count * (int64_t)sizeof(float);
+  if (cudaMalloc(&c->phi, (size_t)c->phi_bytes) != cudaSuccess ||
+      cudaMalloc(&c->h, (size_t)c->h_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return ABG_OK;  // the destructor frees whichever allocation succeeded
+  }
+  ABG_CUDA(cudaMemcpyAsync(c->phi, phi, (size_t)c->phi_bytes, cudaMemcpyDeviceToDevice, s));
+  ABG_CUDA(cudaMemcpyAsync(c->h, h, (size_t)c->h_bytes, cudaMemcpyDeviceToDevice, s));
+  ABG_CUDA(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
+  ABG_CUDA(cudaEventRecord(c->ready, s));
+  std::lock_guard<std::mutex> lk(g->zmu);
+  if (g->phicache) g->footprint -= g->phicache->phi_bytes + g->phicache->h_bytes;
+  g->phicache = c;
+  g->footprint += c->phi_bytes + c->h_bytes;
+  return ABG_OK;
+}
+
 int solve_batch(abg_graph* g, const RowSpace& rs, const std::vector<int>& ks,
                 const std::vector<uint64_t>& seeds, const abg_params& p, int d, SolveOut& o,
                 cudaEvent_t* ev, cudaStream_t s) {
@@ -348,8 +394,23 @@ int solve_batch(abg_graph* g, const RowSpace& rs, const std::vector<int>& ks,
   out.right = H;
   out.ldr = kk;
   out.rseg = hseg;
-  ABG_TRY(rsvd(in, ss, 0, p.power_iters, ABG_STREAM_OMEGA_R, out, o.breakdowns, s));
+  const bool warm = (p.options & ABG_WARM_START) && nseg == 1;
+  if (warm) {
+    std::lock_guard<std::mutex> lk(g->zmu);
+    if (g->phicache && g->phicache->k == kmax && g->phicache->d == d) o.phold = g->phicache;
+  }
+  if (o.phold) {  // Phi, H at the end of an earlier solve's ONMF steps: no seeding (Eq. 18)
+    ABG_CUDA(cudaStreamWaitEvent(s, o.phold->ready, 0));
+    ABG_CUDA(cudaMemcpyAsync(phi, o.phold->phi, (size_t)o.phold->phi_bytes,
+                             cudaMemcpyDeviceToDevice, s));
+    ABG_CUDA(cudaMemcpyAsync(H, o.phold->h, (size_t)o.phold->h_bytes, cudaMemcpyDeviceToDevice,
+                             s));
+    o.warm = 1;
+  } else {
+    ABG_TRY(rsvd(in, ss, 0, p.power_iters, ABG_STREAM_OMEGA_R, out, o.breakdowns, s));
+  }
   ABG_TRY(onmf_iterations(rs, ss, R, m, ldr, p.t_f, phi, kk, H, kk, hseg, s, R16, ldr16));
+  if (warm) ABG_TRY(phicache_store(g, kmax, d, phi, n * kk, H, hseg, s));
   if (ev) ABG_CUDA(cudaEventRecord(ev[4], s));
   // ---- Algorithm 3 ----
   ABG_TRY(nci_run(rs, ss, phi, kk, p.t_g, p.nci_flags, o.labels, nullptr, nullptr, o.counters,
@@ -396,7 +457,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
   for (int i = 0; i < 7; ++i) ev[i] = e[i].e;
   std::vector<double> obj(2 * nseg);
   std::vector<int> cnt(3 * nseg), cl(nseg), passes;
-  int reused = 0;
+  int reused = 0, warm = 0;
   int bd = 0;
   {
     Scratch scr(s);
@@ -421,6 +482,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     }
     passes = o.passes;
     reused = o.reused;
+    warm = o.warm;
     ABG_CUDA(cudaMemcpyAsync(labels, o.labels, sizeof(int32_t) * g->n_u, cudaMemcpyDefault, s));
     ABG_CUDA(cudaMemcpyAsync(obj.data(), o.obj, sizeof(double) * 2 * nseg, cudaMemcpyDeviceToHost, s));
     ABG_CUDA(cudaMemcpyAsync(cnt.data(), o.counters, sizeof(int) * 3 * nseg, cudaMemcpyDeviceToHost, s));
@@ -448,6 +510,7 @@ int cluster_impl(abg_graph* g, const abg_params* ps, int np, cudaStream_t s, int
     r.chol_breakdowns = bd;
     r.nci_passes = i < (int)passes.size() ? passes[i] : ps[i].t_g;
     r.reused_propagation = reused;
+    r.warm_started = warm;
     for (int j = 0; j < 6; ++j) r.ms_phase[j] = ms[j];
     finite &= std::isfinite(r.objective);
     if (res) res[i] = r;
