@@ -149,13 +149,16 @@ __global__ void k_row_scale(const int64_t* __restrict__ ptr, const float* __rest
   const bool valid = row < rows;
   const int64_t b = valid ? ptr[row] : 0, e = valid ? ptr[row + 1] : 0;
   const bool light = e - b <= 32;
+  // weighted rows with more than kHeavyRow edges are summed over their schedule chunks
+  // (k_chunk_wsum, k_heavy_scale), so that a hub is spread over many warps
+  const bool split = w && e - b > kHeavyRow;
   double acc = 0.0;
   if (!w) {
     acc = (double)(e - b);
   } else {
     if (light)
       for (int64_t j = b; j < e; ++j) acc += (double)w[j];
-    unsigned heavy = __ballot_sync(0xffffffffu, valid && !light);
+    unsigned heavy = __ballot_sync(0xffffffffu, valid && !light && !split);
     while (heavy) {
       const int i = __ffs(heavy) - 1;
       heavy &= heavy - 1;
@@ -167,38 +170,92 @@ __global__ void k_row_scale(const int64_t* __restrict__ ptr, const float* __rest
       if (lane == i) acc = part;
     }
   }
-  if (valid) scale[row] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
+  if (valid && !split) scale[row] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
 }
 
-// L values (Eq. 7) of one storage order: val[e] = w[e] * s_row[row] * s_col[col[e]]. A lane
-// takes its own row when it has at most 32 edges, the warp the longer rows together.
-__global__ void k_l_values(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                           const float* __restrict__ w, int64_t rows,
-                           const float* __restrict__ s_row, const float* __restrict__ s_col,
-                           float* __restrict__ val) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t base = row - (threadIdx.x & 31);
+// The rows that k_row_scale leaves (weighted, more than kHeavyRow edges): one warp per
+// schedule chunk sums its weights (lanes over the chunk, then a shuffle tree) ...
+__global__ void k_chunk_wsum(const int64_t* __restrict__ ptr, const float* __restrict__ w,
+                             abg_graph::Schedule sc, double* __restrict__ part) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (base >= rows) return;  // whole warps
-  const bool valid = row < rows;
-  const int64_t b = valid ? ptr[row] : 0, e = valid ? ptr[row + 1] : 0;
-  const bool light = e - b <= 32;
-  const double sr = valid ? (double)s_row[row] : 0.0;
-  if (valid && light)
-    for (int64_t j = b; j < e; ++j) {
+  if (c >= sc.n_chunks) return;  // whole warps
+  const int64_t b = sc.chunk_begin[c];
+  const int row = sc.heavy_row[sc.chunk_row_slot[c]];
+  const int64_t e = min(b + (int64_t)kHeavyChunk, ptr[row + 1]);
+  double acc = 0.0;
+  for (int64_t j = b + lane; j < e; j += 32) acc += (double)w[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) part[c] = acc;
+}
+
+// ... and one thread per such row adds its chunks' sums in chunk order
+__global__ void k_heavy_scale(abg_graph::Schedule sc, const double* __restrict__ part,
+                              float* __restrict__ scale) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= sc.n_heavy) return;
+  double acc = 0.0;
+  for (int64_t c = sc.heavy_chunk0[h]; c < sc.heavy_chunk0[h + 1]; ++c) acc += part[c];
+  scale[sc.heavy_row[h]] = acc > 0.0 ? (float)(1.0 / sqrt(acc)) : 0.0f;
+}
+
+// L values (Eq. 7) of one storage order: val[e] = w[e] * s_row[row] * s_col[col[e]]. A warp
+// takes 32 consecutive rows and walks them one after another, its lanes striding over each
+// row's edges (consecutive edges on consecutive lanes).
+constexpr int kLvWarps = 8;
+
+__global__ void __launch_bounds__(32 * kLvWarps) k_l_values(
+    const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ w, int64_t rows, const float* __restrict__ s_row,
+    const float* __restrict__ s_col, float* __restrict__ val) {
+  __shared__ int64_t start[kLvWarps][33];
+  __shared__ double srow[kLvWarps][32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = ((int64_t)blockIdx.x * kLvWarps + wid) * 32;
+  if (r0 >= rows) return;  // whole warps
+  const int nr = rows - r0 < 32 ? (int)(rows - r0) : 32;
+  start[wid][lane] = ptr[r0 + min(lane, nr)];
+  if (lane == 0) start[wid][32] = ptr[r0 + nr];
+  srow[wid][lane] = lane < nr ? (double)s_row[r0 + lane] : 0.0;
+  __syncwarp();
+  for (int i = 0; i < nr; ++i) {
+    const int64_t e = start[wid][i + 1];
+    if (e - start[wid][i] > kHeavyRow) continue;  // its schedule chunks (k_l_values_chunks)
+    const double sr = srow[wid][i];
+    for (int64_t j = start[wid][i] + lane; j < e; j += 32) {
       const double wj = w ? (double)w[j] : 1.0;
       val[j] = (float)(wj * sr * (double)s_col[col[j]]);
     }
-  unsigned heavy = __ballot_sync(0xffffffffu, valid && !light);
-  while (heavy) {
-    const int i = __ffs(heavy) - 1;
-    heavy &= heavy - 1;
-    const int64_t hb = __shfl_sync(0xffffffffu, b, i), he = __shfl_sync(0xffffffffu, e, i);
-    const double hs = __shfl_sync(0xffffffffu, sr, i);
-    for (int64_t j = hb + lane; j < he; j += 32) {
-      const double wj = w ? (double)w[j] : 1.0;
-      val[j] = (float)(wj * hs * (double)s_col[col[j]]);
-    }
+  }
+}
+
+// L values of the rows with more than kHeavyRow edges: one warp per schedule chunk
+__global__ void k_l_values_chunks(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                  const float* __restrict__ w, abg_graph::Schedule sc,
+                                  const float* __restrict__ s_row,
+                                  const float* __restrict__ s_col, float* __restrict__ val) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= sc.n_chunks) return;  // whole warps
+  const int64_t b = sc.chunk_begin[c];
+  const int row = sc.heavy_row[sc.chunk_row_slot[c]];
+  const int64_t e = min(b + (int64_t)kHeavyChunk, ptr[row + 1]);
+  const double sr = (double)s_row[row];
+  for (int64_t j = b + lane; j < e; j += 32) {
+    const double wj = w ? (double)w[j] : 1.0;
+    val[j] = (float)(wj * sr * (double)s_col[col[j]]);
+  }
+}
+
+// First out-of-range index (first[0]) and first weight that is not finite and positive
+// (first[1]) of an edge array; both stay at nnz when there is none.
+__global__ void k_check_edges(const int32_t* __restrict__ idx, const float* __restrict__ w,
+                              int64_t nnz, int64_t cols, unsigned long long* __restrict__ first) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    if (idx[j] < 0 || idx[j] >= cols) atomicMin(first, (unsigned long long)j);
+    if (w && !(isfinite(w[j]) && w[j] > 0.f)) atomicMin(first + 1, (unsigned long long)j);
   }
 }
 
@@ -266,6 +323,17 @@ static int validate_csr(const int64_t* ptr, const int32_t* idx, const float* w, 
   return ABG_OK;
 }
 
+// The row-pointer half of validate_csr (host); the index and weight half runs on the device
+// (k_check_edges) once the arrays are uploaded.
+static int validate_ptr(const int64_t* ptr, const int32_t* idx, int64_t rows, int64_t nnz,
+                        const char* name) {
+  ABG_CHECK(ptr && idx, "%s: null CSR arrays", name);
+  ABG_CHECK(ptr[0] == 0 && ptr[rows] == nnz, "%s: ptr[0] must be 0 and ptr[rows] = nnz", name);
+  const int64_t r = first_bad(rows, [&](int64_t i) { return ptr[i + 1] < ptr[i]; });
+  ABG_CHECK(r == rows, "%s: ptr not monotone at row %lld", name, (long long)r);
+  return ABG_OK;
+}
+
 // Stable counting sort CSR -> CSC (deterministic edge order inside each column:
 // increasing row), parallel over row ranges with per-thread column offsets.
 static void build_csc(int64_t n_u, int64_t n_v, int64_t nnz, const int64_t* u_ptr,
@@ -326,8 +394,17 @@ int abg::swap_sides(const abg_graph_desc* in, abg::SideSwap* store, const abg_gr
 // Row schedule of one SpMM direction: light rows grouped into tasks of at most
 // kTaskRows consecutive rows and about kTaskEdges edges (a task never spans a
 // heavy row), heavy rows cut into kHeavyChunk-edge chunks.
-static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_graph::Schedule& sc,
-                          cudaStream_t s) {
+// Host half of a row schedule: the task and chunk lists (computed from the host row pointers
+// only, so it can run while the arrays upload).
+struct SchedHost {
+  std::vector<int32_t> tasks, et, zt;  // (first row, one past the last row) pairs
+  std::vector<int64_t> cb;             // chunk starts
+  std::vector<int32_t> cslot;          // heavy slot of each chunk
+  std::vector<int32_t> hrow;           // heavy rows
+  std::vector<int64_t> hc0;            // first chunk of each heavy row (n_heavy + 1)
+};
+
+static void compute_schedule(const int64_t* ptr, int64_t rows, SchedHost& H) {
   // row ranges scanned by several host threads; a task never crosses a range boundary, and
   // results do not depend on task boundaries (every row sums its edges in edge order)
   struct Part {
@@ -380,11 +457,11 @@ static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_gr
     for (int t = 0; t < nt; ++t) th.emplace_back(scan, t);
     for (auto& x : th) x.join();
   }
-  std::vector<int32_t> tasks;
-  std::vector<int64_t> cb;
-  std::vector<int32_t> cslot;
-  std::vector<int32_t> hrow;
-  std::vector<int64_t> hc0;
+  std::vector<int32_t>& tasks = H.tasks;
+  std::vector<int64_t>& cb = H.cb;
+  std::vector<int32_t>& cslot = H.cslot;
+  std::vector<int32_t>& hrow = H.hrow;
+  std::vector<int64_t>& hc0 = H.hc0;
   for (const Part& P : parts) {
     const int32_t slot0 = (int32_t)hrow.size();
     const int64_t chunk0 = (int64_t)cb.size();
@@ -396,12 +473,25 @@ static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_gr
   }
   hc0.push_back((int64_t)cb.size());
   // the same tasks split by whether they hold edges (the TMA-gather kernel takes those that do)
-  std::vector<int32_t> et, zt;
+  std::vector<int32_t>& et = H.et;
+  std::vector<int32_t>& zt = H.zt;
   for (size_t i = 0; i < tasks.size(); i += 2) {
     auto& dst = ptr[tasks[i + 1]] > ptr[tasks[i]] ? et : zt;
     dst.push_back(tasks[i]);
     dst.push_back(tasks[i + 1]);
   }
+}
+
+// Device half: the lists of H into sc (H must stay alive until the copies have run).
+static int upload_schedule(abg_graph* g, const SchedHost& H, abg_graph::Schedule& sc,
+                           cudaStream_t s) {
+  const std::vector<int32_t>& tasks = H.tasks;
+  const std::vector<int32_t>& et = H.et;
+  const std::vector<int32_t>& zt = H.zt;
+  const std::vector<int64_t>& cb = H.cb;
+  const std::vector<int32_t>& cslot = H.cslot;
+  const std::vector<int32_t>& hrow = H.hrow;
+  const std::vector<int64_t>& hc0 = H.hc0;
   sc.n_tasks = (int64_t)tasks.size() / 2;
   sc.n_etasks = (int64_t)et.size() / 2;
   sc.n_ztasks = (int64_t)zt.size() / 2;
@@ -441,8 +531,6 @@ static int build_schedule(abg_graph* g, const int64_t* ptr, int64_t rows, abg_gr
   }
   ABG_CUDA(cudaMemcpyAsync(sc.heavy_chunk0, hc0.data(), sizeof(int64_t) * (sc.n_heavy + 1),
                            cudaMemcpyHostToDevice, s));
-  // the host vectors must outlive the copies
-  ABG_CUDA(cudaStreamSynchronize(s));
   return ABG_OK;
 }
 
@@ -522,8 +610,13 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
   g->nnz = d->nnz;
   g->d_u = d->d_u;
   g->x_kind = d->x_kind;
-  ABG_TRY(validate_csr(d->u_ptr, d->v_idx, d->w, d->n_u, d->n_v, d->nnz, "CSR"));
   const bool have_csc = d->v_ptr || d->u_idx || d->w_t;
+  // with a caller-given CSC the edge arrays are checked on the device after the upload (before
+  // any kernel indexes with them); building the CSC here needs them checked first
+  if (have_csc)
+    ABG_TRY(validate_ptr(d->u_ptr, d->v_idx, d->n_u, d->nnz, "CSR"));
+  else
+    ABG_TRY(validate_csr(d->u_ptr, d->v_idx, d->w, d->n_u, d->n_v, d->nnz, "CSR"));
   std::vector<int64_t> vp;
   std::vector<int32_t> ui;
   std::vector<float> wt;
@@ -533,13 +626,25 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
   if (have_csc) {
     ABG_CHECK(d->v_ptr && d->u_idx && (!d->w == !d->w_t),
               "CSC needs v_ptr, u_idx and (w_t iff w)");
-    ABG_TRY(validate_csr(d->v_ptr, d->u_idx, d->w_t, d->n_v, d->n_u, d->nnz, "CSC"));
+    ABG_TRY(validate_ptr(d->v_ptr, d->u_idx, d->n_v, d->nnz, "CSC"));
   } else {
     build_csc(d->n_u, d->n_v, d->nnz, d->u_ptr, d->v_idx, d->w, vp, ui, wt);
     v_ptr = vp.data();
     u_idx = ui.data();
     w_t = d->w ? wt.data() : nullptr;
   }
+  // the row schedules need only the host row pointers: computed while the arrays upload
+  SchedHost sh_u, sh_v;
+  std::thread sched_thread([&] {
+    compute_schedule(d->u_ptr, d->n_u, sh_u);
+    compute_schedule(v_ptr, d->n_v, sh_v);
+  });
+  struct Joiner {
+    std::thread& t;
+    ~Joiner() {
+      if (t.joinable()) t.join();
+    }
+  } joiner{sched_thread};
   // attributes
   if (d->x_kind == ABG_X_CSR_F32) {
     ABG_TRY(validate_csr(d->x_ptr, d->x_idx, nullptr, d->n_u, d->d_u, d->x_ptr ? d->x_ptr[d->n_u] : 0,
@@ -566,6 +671,31 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
     ABG_CUDA(cudaMemcpyAsync(w_dev, d->w, sizeof(float) * d->nnz, cudaMemcpyHostToDevice, s));
     ABG_CUDA(cudaMemcpyAsync(wt_dev, w_t, sizeof(float) * d->nnz, cudaMemcpyHostToDevice, s));
   }
+  if (have_csc && d->nnz) {  // indices in range and weights finite and positive, both orders
+    unsigned long long* first;
+    ABG_TRY(scr.get(&first, 4));
+    const unsigned long long init[4] = {(unsigned long long)d->nnz, (unsigned long long)d->nnz,
+                                        (unsigned long long)d->nnz, (unsigned long long)d->nnz};
+    ABG_CUDA(cudaMemcpyAsync(first, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(d->nnz, 256), num_sms() * 8);
+    k_check_edges<<<grid, 256, 0, s>>>(g->u_col, w_dev, d->nnz, d->n_v, first);
+    ::abg::note_launch();
+    k_check_edges<<<grid, 256, 0, s>>>(g->v_col, wt_dev, d->nnz, d->n_u, first + 2);
+    ::abg::note_launch();
+    ABG_LAUNCH_CHECK();
+    unsigned long long hf[4];
+    ABG_CUDA(cudaMemcpyAsync(hf, first, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    ABG_CUDA(cudaStreamSynchronize(s));
+    const int64_t nz = d->nnz;
+    ABG_CHECK((int64_t)hf[0] == nz, "CSR: index %d out of range at %lld", d->v_idx[hf[0]],
+              (long long)hf[0]);
+    ABG_CHECK((int64_t)hf[1] == nz, "CSR: weight %g at %lld not finite/positive",
+              (double)d->w[hf[1]], (long long)hf[1]);
+    ABG_CHECK((int64_t)hf[2] == nz, "CSC: index %d out of range at %lld", d->u_idx[hf[2]],
+              (long long)hf[2]);
+    ABG_CHECK((int64_t)hf[3] == nz, "CSC: weight %g at %lld not finite/positive",
+              (double)d->w_t[hf[3]], (long long)hf[3]);
+  }
   void* p;
   ABG_TRY(graph_alloc(g, &p, sizeof(float) * std::max<int64_t>(1, d->nnz), s));
   g->u_val = (float*)p;
@@ -589,12 +719,47 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
     ABG_CUDA(cudaStreamSynchronize(s));
     ABG_CHECK(hbad == 0, "CSC does not match the CSR (%d columns differ)", hbad);
   }
+  // row schedules first: their chunks of the rows with more than kHeavyRow edges spread those
+  // rows over many warps in the scales and L values below
+  sched_thread.join();
+  ABG_TRY(upload_schedule(g, sh_u, g->sched_u, s));
+  ABG_TRY(upload_schedule(g, sh_v, g->sched_v, s));
   k_row_scale<<<ceil_div(d->n_u, 256), 256, 0, s>>>(g->u_ptr, w_dev, d->n_u, g->su); ::abg::note_launch();
   k_row_scale<<<ceil_div(d->n_v, 256), 256, 0, s>>>(g->v_ptr, wt_dev, d->n_v, g->sv); ::abg::note_launch();
-  k_l_values<<<ceil_div(d->n_u, 256), 256, 0, s>>>(g->u_ptr, g->u_col, w_dev, d->n_u, g->su,
-                                                    g->sv, g->u_val); ::abg::note_launch();
-  k_l_values<<<ceil_div(d->n_v, 256), 256, 0, s>>>(g->v_ptr, g->v_col, wt_dev, d->n_v, g->sv,
-                                                    g->su, g->v_val); ::abg::note_launch();
+  if (d->w) {
+    double* part;
+    ABG_TRY(scr.get(&part, (size_t)std::max<int64_t>(
+                               1, std::max(g->sched_u.n_chunks, g->sched_v.n_chunks))));
+    const struct {
+      const int64_t* ptr;
+      const float* w;
+      const abg_graph::Schedule* sc;
+      float* scale;
+    } sides[2] = {{g->u_ptr, w_dev, &g->sched_u, g->su}, {g->v_ptr, wt_dev, &g->sched_v, g->sv}};
+    for (const auto& sd : sides) {
+      if (sd.sc->n_chunks == 0) continue;
+      k_chunk_wsum<<<(unsigned)ceil_div(sd.sc->n_chunks, 8), 256, 0, s>>>(sd.ptr, sd.w, *sd.sc,
+                                                                          part);
+      ::abg::note_launch();
+      k_heavy_scale<<<(unsigned)ceil_div(sd.sc->n_heavy, 256), 256, 0, s>>>(*sd.sc, part,
+                                                                            sd.scale);
+      ::abg::note_launch();
+    }
+  }
+  k_l_values<<<ceil_div(d->n_u, 32 * kLvWarps), 32 * kLvWarps, 0, s>>>(
+      g->u_ptr, g->u_col, w_dev, d->n_u, g->su, g->sv, g->u_val); ::abg::note_launch();
+  k_l_values<<<ceil_div(d->n_v, 32 * kLvWarps), 32 * kLvWarps, 0, s>>>(
+      g->v_ptr, g->v_col, wt_dev, d->n_v, g->sv, g->su, g->v_val); ::abg::note_launch();
+  if (g->sched_u.n_chunks) {
+    k_l_values_chunks<<<(unsigned)ceil_div(g->sched_u.n_chunks, 8), 256, 0, s>>>(
+        g->u_ptr, g->u_col, w_dev, g->sched_u, g->su, g->sv, g->u_val);
+    ::abg::note_launch();
+  }
+  if (g->sched_v.n_chunks) {
+    k_l_values_chunks<<<(unsigned)ceil_div(g->sched_v.n_chunks, 8), 256, 0, s>>>(
+        g->v_ptr, g->v_col, wt_dev, g->sched_v, g->sv, g->su, g->v_val);
+    ::abg::note_launch();
+  }
   ABG_LAUNCH_CHECK();
 
   // attributes on the device
@@ -626,8 +791,6 @@ static int create_impl(const abg_graph_desc* d, cudaStream_t s, abg_graph* g) {
       ABG_TRY(upload(g, &g->xr_col, xr.data(), g->x_nnz, s));
     ABG_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   }
-  ABG_TRY(build_schedule(g, d->u_ptr, d->n_u, g->sched_u, s));
-  ABG_TRY(build_schedule(g, v_ptr, d->n_v, g->sched_v, s));
   {
     void* p;
     ABG_TRY(graph_alloc(g, &p, sizeof(int), s));

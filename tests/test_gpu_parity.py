@@ -315,6 +315,39 @@ def test_invalid_parameters_rejected():
     h.close()
 
 
+def _csc(g):
+    order = np.argsort(g.v_idx, kind="stable")
+    v_ptr = np.zeros(g.n_v + 1, dtype=np.int64)
+    np.cumsum(np.bincount(g.v_idx, minlength=g.n_v), out=v_ptr[1:])
+    rows = np.repeat(np.arange(g.n_u, dtype=np.int32), np.diff(g.u_ptr))
+    return v_ptr, rows[order].copy(), g.w[order].copy()
+
+
+def test_invalid_edges_rejected_with_a_given_csc():
+    # with the CSC given, the edge indices and weights of both orders are checked on the
+    # device after the upload, before any kernel indexes with them; a good graph creates
+    g = synth.make_small(11, n_u=500, n_v=700, k=3, d_u=4, deg=6)
+    abg.abg_create(g, csc=_csc(g)).close()
+    cases = []
+    v_ptr, u_idx, w_t = _csc(g)
+    bad = u_idx.copy(); bad[17] = g.n_u + 3
+    cases.append(("CSC: index", g, (v_ptr, bad, w_t)))
+    bad = w_t.copy(); bad[5] = -1.0
+    cases.append(("CSC: weight", g, (v_ptr, u_idx, bad)))
+    g2 = synth.make_small(11, n_u=500, n_v=700, k=3, d_u=4, deg=6)
+    g2.v_idx = g2.v_idx.copy(); g2.v_idx[40] = -2
+    cases.append(("CSR: index", g2, _csc(g)))
+    g3 = synth.make_small(11, n_u=500, n_v=700, k=3, d_u=4, deg=6)
+    g3.w = g3.w.copy(); g3.w[9] = float("nan")
+    cases.append(("CSR: weight", g3, _csc(g)))
+    for what, gg, csc in cases:
+        with pytest.raises(abg.AbgError) as e:
+            abg.abg_create(gg, csc=csc)
+        assert e.value.status == abg.ABG_EINVAL, what
+        assert what in str(e.value), (what, str(e.value))
+    abg.abg_create(g, csc=_csc(g)).close()   # the device is fine afterwards
+
+
 def _nan_padded(a: np.ndarray):
     """Device copy of `a` whose row padding (columns width..ld-1) holds NaN."""
     t = dev(a)
