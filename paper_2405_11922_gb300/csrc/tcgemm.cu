@@ -1009,6 +1009,7 @@ struct Tn2Args {
   int nops;
   uint32_t op_bytes;
   uint32_t stage_bytes;  // one staging slot: transposing threads x units x 64 bytes
+  int syrk;              // A == B (a Gram matrix): B's operand is the first Np rows of A's
   uint32_t acc_cols;     // TMEM columns of one accumulator (>= mblk * Np)
   uint32_t tmem_cols;
   int* wait_err;
@@ -1091,8 +1092,9 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
           }
           tc_fence_after();
           const uint32_t ob = smem_addr(ops + (size_t)os * p.op_bytes);
-          const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes, b_hi = ob + 2 * a_hi_bytes,
-                         b_lo = b_hi + b_hi_bytes;
+          const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes,
+                         b_hi = p.syrk ? a_hi : ob + 2 * a_hi_bytes,
+                         b_lo = p.syrk ? a_lo : b_hi + b_hi_bytes;
           for (int mb = 0; mb < p.mblk; ++mb) {
             const uint32_t dcol = acc + (uint32_t)(mb * p.Np);
             const uint32_t ao = (uint32_t)mb * kTcM * 128;
@@ -1160,7 +1162,7 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
     // different 16-byte chunks of the 128-byte swizzle row, no bank conflict.
     // A thread's units are the same for every block; which block they read changes.
     const uint32_t na4 = a_rows / 4, nb4 = (uint32_t)p.Np / 4;
-    const uint32_t ua = ((na4 + 3) / 4) * 32, ub = ((nb4 + 3) / 4) * 32;
+    const uint32_t ua = ((na4 + 3) / 4) * 32, ub = p.syrk ? 0u : ((nb4 + 3) / 4) * 32;
     constexpr int kMaxU = kTn2Units;  // units per thread (A and B together), checked at launch
     int uc0[kMaxU], uk4[kMaxU], uwhich[kMaxU];
 #pragma unroll
@@ -1885,9 +1887,13 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.Np = (int)round_up(a.N, 16);
   p.mblk = (int)ceil_div(a.K, kTcM);
   if (p.Np > 128 || p.mblk > 2) return ABG_OK;
+  // a Gram matrix (A == B, K == N <= 128): B's operand is the first Np rows of A's, so B is
+  // neither staged nor transposed
+  p.syrk = a.A == a.B && a.K == a.N && a.lda == a.ldb && a.segK == a.segN && p.mblk == 1;
   // units per transposing thread: A (mblk 128 / 4 column groups) and B (Np / 4), x 8 row
   // groups, in warps of 4 column groups (k_tc_tn2 holds at most kTn2Units per thread)
-  const int64_t units = ceil_div(p.mblk * kTcM / 4, 4) * 32 + ceil_div(p.Np / 4, 4) * 32;
+  const int64_t units =
+      ceil_div(p.mblk * kTcM / 4, 4) * 32 + (p.syrk ? 0 : ceil_div(p.Np / 4, 4) * 32);
   if (units > kTn2Units * 32 * TW) return ABG_OK;
   const int U = (int)ceil_div(units, 32 * TW);  // units per transposing thread
   p.stage_bytes = 32u * TW * (uint32_t)U * 64u;
@@ -1902,7 +1908,7 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.chunk_row0 = rs.chunk_row0;
   p.chunk_rows = rs.chunk_rows;
   p.part = part;
-  p.op_bytes = 2u * p.mblk * kTcM * 128 + 2u * p.Np * 128;
+  p.op_bytes = 2u * p.mblk * kTcM * 128 + (p.syrk ? 0u : 2u * p.Np * 128);
   p.acc_cols = 32;
   while ((int)p.acc_cols < p.mblk * p.Np) p.acc_cols *= 2;
   p.tmem_cols = 2 * p.acc_cols;
