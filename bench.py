@@ -173,7 +173,10 @@ def roofline_of(pbytes: float, prop_ms: float, peak: float, peak_kind: str, scal
            "frac": achieved / peak, "traffic": None,
            "kernel": "propagation SpMMs per round (k_spmm_tma light tasks + heavy-row chunks, "
                      "k_spmm_reduce)",
-           "per": "propagation round", "algorithmic_bytes": pbytes / gamma, "peak_kind": peak_kind}
+           "per": "propagation round", "algorithmic_bytes": pbytes / gamma, "peak_kind": peak_kind,
+           "note": "frac counts every gathered row once per edge, so L2 hits on hub rows can take "
+                   "it above 1; traffic_frac (measured DRAM bytes of a round over the same time) "
+                   "is the share of HBM bandwidth the round uses"}
     if scale == 1.0 and precision == "fp32":
         out["traffic"] = ROUND_DRAM_BYTES_FULL
         out["traffic_gbs"] = ROUND_DRAM_BYTES_FULL / round_s / 1e9
