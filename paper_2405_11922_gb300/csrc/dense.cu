@@ -560,7 +560,15 @@ __global__ void k_rf_normalise(int64_t n, int w2, float* __restrict__ R, int64_t
     double dot = (double)hi + (double)lo;
     clamp = !(dot > 1e-300);
     if (clamp) dot = 1e-300;
-    inv = (float)(1.0 / sqrt(dot));
+    if (dot > 1e-30 && dot < 1e30) {
+      // FP32 reciprocal square root and one Newton step (about 1 ulp): an FP64 square root
+      // and division per row would occupy the SM's narrow FP64 unit for ~2 ms at 2M rows
+      const float df = (float)dot;
+      const float y = rsqrtf(df);
+      inv = y * fmaf(-0.5f * df * y, y, 1.5f);
+    } else {
+      inv = (float)(1.0 / sqrt(dot));
+    }
   }
   inv = __shfl_sync(0xffffffffu, inv, 0);
 #pragma unroll

@@ -930,20 +930,24 @@ __global__ void k_colsign(const int* __restrict__ segk, int kfix, int kmax,
   }
 }
 
-// G[i][j] <- sign_s[j] G[i][j] (then max(., 0) with relu) for j < k_s of the row's segment
+// G[i][j] <- sign_s[j] G[i][j] (then max(., 0) with relu) for j < k_s of the row's segment;
+// one warp per row, the lanes over its columns
 __global__ void k_apply_sign(int64_t rows, const int* __restrict__ row_seg,
                              const int* __restrict__ segk, int kfix, int kmax,
                              const float* __restrict__ sign, int relu, float* __restrict__ G,
                              int64_t ldg) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= rows * kmax) return;
-  const int64_t i = q / kmax;
-  const int j = (int)(q % kmax);
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= rows) return;
   const int sg = row_seg[i];
-  if (j >= (segk ? segk[sg] : kfix)) return;
-  float v = G[i * ldg + j] * sign[(int64_t)sg * kmax + j];
-  if (relu) v = fmaxf(v, 0.f);
-  G[i * ldg + j] = v;
+  const int k = segk ? segk[sg] : kfix;
+  const float* sgn = sign + (int64_t)sg * kmax;
+  float* g = G + i * ldg;
+  for (int j = lane; j < k; j += 32) {
+    float v = g[j] * sgn[j];
+    if (relu) v = fmaxf(v, 0.f);
+    g[j] = v;
+  }
 }
 
 // Uks_s[p][j] *= sign_s[j]: the right factor follows the left one's sign
@@ -1118,7 +1122,7 @@ int rsvd(const RsvdIn& in, const SegSizes& ss, int kfixed, int power_iters, int 
     k_colsign<<<(unsigned)nseg, 128, 0, s>>>(segk, kfixed, kmax, rs.seg_group0, rs.group_chunk0,
                                              rs.group_nchunks, part, sign);
     note_launch();
-    k_apply_sign<<<(unsigned)ceil_div(rs.rows * kmax, 256), 256, 0, s>>>(
+    k_apply_sign<<<(unsigned)ceil_div(rs.rows, 8), 256, 0, s>>>(
         rs.rows, rs.row_seg, segk, kfixed, kmax, sign, out.left_mode == 0 ? 1 : 0, out.left,
         out.ldl);
     note_launch();
