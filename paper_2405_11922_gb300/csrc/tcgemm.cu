@@ -1010,6 +1010,7 @@ struct Tn2Args {
   uint32_t op_bytes;
   uint32_t stage_bytes;  // one staging slot: transposing threads x units x 64 bytes
   int syrk;              // A == B (a Gram matrix): B's operand is the first Np rows of A's
+  int swap;              // K > 128: B's 128 operand rows are the MMA's M, A's 256 its N
   uint32_t acc_cols;     // TMEM columns of one accumulator (>= mblk * Np)
   uint32_t tmem_cols;
   int* wait_err;
@@ -1043,7 +1044,8 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 2 * (size_t)p.stage_bytes);
   const uint32_t opfull0 = smem_addr(bars), opempty0 = opfull0 + 8 * NO,
                  tfull0 = opempty0 + 8 * NO, tempty0 = tfull0 + 16, drain = tempty0 + 16;
-  const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128, b_hi_bytes = (uint32_t)p.Np * 128;
+  const uint32_t a_hi_bytes = (uint32_t)p.mblk * kTcM * 128,
+                 b_hi_bytes = (uint32_t)(p.swap ? kTcM : p.Np) * 128;
   if (threadIdx.x == 0) {
     for (int i = 0; i < NO; ++i) {
       mbar_init(opfull0 + 8 * i, TW);  // one arrival per transposing warp
@@ -1071,7 +1073,7 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
 
   if (warp == 0) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = tf32_idesc(p.Np);
+      const uint32_t idesc = tf32_idesc(p.swap ? p.mblk * kTcM : p.Np);
       int os = 0;
       uint32_t op_ph = 0;
       int it = 0;
@@ -1095,16 +1097,27 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
           const uint32_t a_hi = ob, a_lo = ob + a_hi_bytes,
                          b_hi = p.syrk ? a_hi : ob + 2 * a_hi_bytes,
                          b_lo = p.syrk ? a_lo : b_hi + b_hi_bytes;
-          for (int mb = 0; mb < p.mblk; ++mb) {
-            const uint32_t dcol = acc + (uint32_t)(mb * p.Np);
-            const uint32_t ao = (uint32_t)mb * kTcM * 128;
+          if (p.swap) {
+            // D^T (B's columns x A's 256 columns) in one MMA per term and K step
 #pragma unroll
             for (int j = 0; j < kTnRows / 8; ++j) {
               const uint32_t off = 32u * j;
-              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_hi + off), idesc,
-                       (b | j) != 0);
-              mma_tf32(dcol, sw128_desc(a_lo + ao + off), sw128_desc(b_hi + off), idesc, 1u);
-              mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_lo + off), idesc, 1u);
+              mma_tf32(acc, sw128_desc(b_hi + off), sw128_desc(a_hi + off), idesc, (b | j) != 0);
+              mma_tf32(acc, sw128_desc(b_hi + off), sw128_desc(a_lo + off), idesc, 1u);
+              mma_tf32(acc, sw128_desc(b_lo + off), sw128_desc(a_hi + off), idesc, 1u);
+            }
+          } else {
+            for (int mb = 0; mb < p.mblk; ++mb) {
+              const uint32_t dcol = acc + (uint32_t)(mb * p.Np);
+              const uint32_t ao = (uint32_t)mb * kTcM * 128;
+#pragma unroll
+              for (int j = 0; j < kTnRows / 8; ++j) {
+                const uint32_t off = 32u * j;
+                mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_hi + off), idesc,
+                         (b | j) != 0);
+                mma_tf32(dcol, sw128_desc(a_lo + ao + off), sw128_desc(b_hi + off), idesc, 1u);
+                mma_tf32(dcol, sw128_desc(a_hi + ao + off), sw128_desc(b_lo + off), idesc, 1u);
+              }
             }
           }
           issued = true;
@@ -1269,17 +1282,31 @@ __global__ void __maxnreg__(128) k_tc_tn2(const Tn2Args p, int64_t n_chunks) {
       if (bad) break;
       tc_fence_after();
       float* pc = p.part + c * (int64_t)p.K * p.N;
-      for (int mb = 0; mb < p.mblk; ++mb) {
-        const int ka = mb * kTcM + quad * 32 + lane;
-        for (int c0 = 0; c0 < p.Np; c0 += 32) {
+      if (p.swap) {
+        // this lane's accumulator row is B's column n; its columns are A's columns ka
+        const int n = quad * 32 + lane;
+        for (int c0 = 0; c0 < p.mblk * kTcM; c0 += 32) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) +
-                        (uint32_t)(abuf * p.acc_cols + mb * p.Np + c0), v);
-          if (ka >= p.K) continue;
-          float* prow = pc + (int64_t)ka * p.N;
+          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(abuf * p.acc_cols + c0),
+                    v);
+          if (n >= p.N) continue;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (c0 + j < p.N) prow[c0 + j] = v[j];
+            if (c0 + j < p.K) pc[(int64_t)(c0 + j) * p.N + n] = v[j];
+        }
+      } else {
+        for (int mb = 0; mb < p.mblk; ++mb) {
+          const int ka = mb * kTcM + quad * 32 + lane;
+          for (int c0 = 0; c0 < p.Np; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) +
+                          (uint32_t)(abuf * p.acc_cols + mb * p.Np + c0), v);
+            if (ka >= p.K) continue;
+            float* prow = pc + (int64_t)ka * p.N;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < p.N) prow[c0 + j] = v[j];
+          }
         }
       }
       tc_fence_before();
@@ -1877,6 +1904,15 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   return ABG_OK;
 }
 
+// ABG_TC_TN_SWAP=0 keeps the two 128-row M blocks for K > 128
+static bool swap_off() {
+  static const bool off = [] {
+    const char* e = std::getenv("ABG_TC_TN_SWAP");
+    return e && e[0] == '0';
+  }();
+  return off;
+}
+
 // k_tc_tn2 for N <= 128 when two operand sets fit; false in *used otherwise
 static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_t s, bool* used) {
   constexpr int TW = 8;
@@ -1908,9 +1944,13 @@ static int tc_gemm_tn2(const RowSpace& rs, const TN& a, float* part, cudaStream_
   p.chunk_row0 = rs.chunk_row0;
   p.chunk_rows = rs.chunk_rows;
   p.part = part;
-  p.op_bytes = 2u * p.mblk * kTcM * 128 + (p.syrk ? 0u : 2u * p.Np * 128);
+  // K > 128: one MMA per term covers both 128-column halves of A when B (<= 128 columns, its
+  // operand padded to 128 rows) takes the MMA's M and A's 256 columns its N
+  p.swap = p.mblk == 2 && !p.syrk && !swap_off();
+  p.op_bytes = 2u * p.mblk * kTcM * 128 +
+               (p.syrk ? 0u : 2u * (uint32_t)(p.swap ? kTcM : p.Np) * 128);
   p.acc_cols = 32;
-  while ((int)p.acc_cols < p.mblk * p.Np) p.acc_cols *= 2;
+  while ((int)p.acc_cols < (p.swap ? p.mblk * kTcM : p.mblk * p.Np)) p.acc_cols *= 2;
   p.tmem_cols = 2 * p.acc_cols;
   if (p.tmem_cols > 512) return ABG_OK;
   size_t smem = 0;
