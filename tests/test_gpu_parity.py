@@ -304,6 +304,27 @@ def test_edge_cases_end_to_end():
         assert res.objective == pytest.approx(ref["objective"], rel=1e-5, abs=1e-9)
 
 
+
+def test_graph_without_edges_end_to_end():
+    # every U node isolated: Z = (1 - alpha) X (Eq. 6 with L = 0, scales 0 by reading R2), so
+    # the solve clusters the normalised attributes alone
+    g = synth.make_small(11, n_u=30, n_v=40, k=3, d_u=4, isolated_u=30)
+    assert g.u_ptr[-1] == 0
+    p = dict(k=3, alpha=0.6, gamma=3, d=4, t_f=3, t_g=4, seed=1)
+    labels, res, ref, sure = _end_to_end(g, p)
+    assert np.array_equal(labels[sure], ref["labels"][sure])
+    assert res.objective == pytest.approx(ref["objective"], rel=1e-5)
+
+
+def test_single_node_end_to_end():
+    # one U node and k = 1: every step runs on one row (a single tile with a 127-row ragged
+    # tail, l = 1 in the randomized SVD), the label is 0 and Eq. 8 is 0
+    g = synth.make_small(11, n_u=1, n_v=5, k=1, d_u=3)
+    p = dict(k=1, alpha=0.6, gamma=3, d=3, t_f=3, t_g=4, seed=1)
+    labels, res, ref, _ = _end_to_end(g, p)
+    assert labels.tolist() == [0] and ref["labels"].tolist() == [0]
+    assert res.objective == pytest.approx(ref["objective"], abs=1e-9)
+
 def test_invalid_parameters_rejected():
     g = synth.make_small(10)
     h = abg.abg_create(g)
