@@ -72,6 +72,7 @@ struct TcArgs {
   uint32_t b_bytes;
   uint32_t tmem_cols;
   int b_resident;  // BF16 kernel: all K blocks of B stay in shared memory (one segment)
+  int aux_vec;     // aux / aux2 rows start on 16 bytes (the Phi rule loads them 4 at a time)
   int* wait_err;   // device flag of the solve (or the process-wide one): a wait ran out
   // random features (Eq. 13): C[i][n] = out_scale sin(in_scale acc), C[i][N + n] = ... cos,
   // and per-tile FP64 column sums of both halves into colsum[tile][2N]
@@ -309,8 +310,39 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
     float v[32];
     tmem_ld32(tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
     if (!valid) continue;
-    {
-      float* crow = p.C + gm * p.ldc;
+    if (p.epi == (int)Epi::PhiUpdate) {
+      // Phi rule (Eq. 17): this row's P and Phi values of the chunk are all requested before
+      // any is used (16 at a time, 16-byte loads where four columns are in range), so their
+      // memory latencies overlap instead of following one another
+      const float* prow = p.aux + gm * p.ldaux + c0;
+      const float* qrow = p.aux2 + gm * p.ldaux2 + c0;
+#pragma unroll
+      for (int h = 0; h < 32; h += 16) {
+        float pv[16], ph[16];
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const int gn = c0 + h + j;
+          if (p.aux_vec && gn + 3 < Ns) {
+            const float4 a = *reinterpret_cast<const float4*>(prow + h + j);
+            const float4 b = *reinterpret_cast<const float4*>(qrow + h + j);
+            pv[j] = a.x, pv[j + 1] = a.y, pv[j + 2] = a.z, pv[j + 3] = a.w;
+            ph[j] = b.x, ph[j + 1] = b.y, ph[j + 2] = b.z, ph[j + 3] = b.w;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              pv[j + q] = gn + q < Ns ? prow[h + j + q] : 0.f;
+              ph[j + q] = gn + q < Ns ? qrow[h + j + q] : 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float x = v[h + j];
+          if (c0 + h + j < Ns) v[h + j] = x > 0.f ? ph[j] * sqrtf(fmaxf(pv[j], 0.f) / x) : 0.f;
+        }
+      }
+    } else {
+      // the other epilogues read nothing per element but the sign vector
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int gn = c0 + j;
@@ -320,17 +352,14 @@ __device__ __forceinline__ void tc_epilogue_row(const TcArgs& p, uint32_t tacc, 
             case (int)Epi::Relu: x = fmaxf(x, 0.f); break;
             case (int)Epi::SignRelu: x = fmaxf(p.sign[sg * p.sign_seg + gn] * x, 0.f); break;
             case (int)Epi::Sign: x = p.sign[sg * p.sign_seg + gn] * x; break;
-            case (int)Epi::PhiUpdate: {
-              const float pv = p.aux[gm * p.ldaux + gn];
-              const float phi = p.aux2[gm * p.ldaux2 + gn];
-              x = x > 0.f ? phi * sqrtf(fmaxf(pv, 0.f) / x) : 0.f;
-              break;
-            }
             default: break;
           }
         }
         v[j] = x;
       }
+    }
+    {
+      float* crow = p.C + gm * p.ldc;
       // 16-byte stores where four columns are in range (ldc is a multiple of 4)
 #pragma unroll
       for (int j = 0; j < 32; j += 4) {
@@ -1854,6 +1883,9 @@ int tc_gemm_nn(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   p.ldaux = a.ldaux;
   p.aux2 = a.aux2;
   p.ldaux2 = a.ldaux2;
+  p.aux_vec = a.ldaux % 4 == 0 && a.ldaux2 % 4 == 0 &&
+              reinterpret_cast<uintptr_t>(a.aux) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(a.aux2) % 16 == 0;
   p.sign = a.sign;
   p.sign_seg = a.sign_seg;
   p.labels = a.labels;
@@ -2104,6 +2136,9 @@ int tc_gemm_nn16(const RowSpace& rs, const NN& a, cudaStream_t s, bool* used) {
   p.ldaux = a.ldaux;
   p.aux2 = a.aux2;
   p.ldaux2 = a.ldaux2;
+  p.aux_vec = a.ldaux % 4 == 0 && a.ldaux2 % 4 == 0 &&
+              reinterpret_cast<uintptr_t>(a.aux) % 16 == 0 &&
+              reinterpret_cast<uintptr_t>(a.aux2) % 16 == 0;
   p.sign = a.sign;
   p.sign_seg = a.sign_seg;
   p.b_bytes = (uint32_t)Np * 128;  // one 64-wide K block of B
